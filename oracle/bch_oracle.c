@@ -1,0 +1,1191 @@
+/*
+ * bch_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct FP64 CPU restatement of what the decoder library
+ * computes, written from arXiv 2412.20828 ("Effective Application of Normalized
+ * Min-Sum Decoding for Short BCH Codes", Li & Yu).  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark load this file; the product path
+ * (the CUDA library) never does, and the two share no code, header or table.
+ *
+ * Style on purpose: one byte per bit, dense M x n matrices, direct loops, the
+ * check-to-variable minimum recomputed over "all other edges" (no min1/min2 trick),
+ * no bit packing, no fusion.  Floating point is double; the only FP32 values are the
+ * channel LLRs (the decoder's input format) and the LLRs the frame generator emits.
+ *
+ * Parity status of each function (pins are in tests/test_oracle_*.py):
+ *   or_gen_poly, or_std_h, or_encode  pinned: Table I standard-H attributes, deg g,
+ *                                     roots of g, (15,7) weight distribution.
+ *   or_channel_llr                    pinned: closed form of Eq. (1).
+ *   or_build_ho                       pinned by invariants (dual codewords, rank n-k,
+ *                                     minimum row weight = dual minimum weight, the
+ *                                     (63,45) three-class result of Sec. III-A).  The
+ *                                     exact row SET is parity unpinned against the
+ *                                     paper: its heuristic is under-specified and the
+ *                                     tie-breaking, padding and annealing details are
+ *                                     this library's reading.
+ *   or_draw_autos                     pinned: maps codewords to codewords.
+ *   or_nms_plain                      pinned: hand-derived Eqs. (2)-(4) examples,
+ *                                     noiseless single-iteration decode.
+ *   or_nms_enhanced                   pinned: hand-derived Algorithm 1 example,
+ *                                     permutation equivariance, noiseless decode.
+ *   or_osd                            pinned: order K equals exhaustive ML on (15,7),
+ *                                     most-reliable basis equals the greedy
+ *                                     generator-side basis.
+ *   or_ml                             pinned: corrects every <= t error pattern.
+ *   or_nms_train_grad                 pinned: central finite differences.
+ *   or_philox4x32_10                  pinned: published known-answer vectors.
+ *   or_splitmix64                     pinned: published first output.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 or_u128;
+
+/* Status codes (oracle-local; deliberately not the library's enum). */
+#define OR_OK 0
+#define OR_EARG -1
+#define OR_ECODE -2
+#define OR_ERANK -3
+#define OR_ENOMEM -4
+
+/* ------------------------------------------------------------------------------
+ * GF(2^m) arithmetic with the primitive polynomials named for the workloads:
+ * x^4+x+1 (n=15), x^6+x+1 (n=63), x^7+x^3+1 (n=127).
+ * ---------------------------------------------------------------------------- */
+typedef struct {
+  int m, n, prim;
+  int expt[256];
+  int logt[256];
+} or_gf;
+
+static int gf_setup(or_gf *g, int n) {
+  int m, prim;
+  if (n == 15) {
+    m = 4; prim = 0x13;
+  } else if (n == 63) {
+    m = 6; prim = 0x43;
+  } else if (n == 127) {
+    m = 7; prim = 0x89;
+  } else {
+    return OR_EARG;
+  }
+  g->m = m; g->n = n; g->prim = prim;
+  for (int i = 0; i < 256; i++) g->logt[i] = -1;
+  int x = 1;
+  for (int i = 0; i < n; i++) {
+    g->expt[i] = x;
+    g->logt[x] = i;
+    x <<= 1;
+    if (x & (1 << m)) x ^= prim;
+  }
+  return OR_OK;
+}
+
+static int gf_mul(const or_gf *g, int a, int b) {
+  if (a == 0 || b == 0) return 0;
+  return g->expt[(g->logt[a] + g->logt[b]) % g->n];
+}
+
+/* Multiplicative order of 2 modulo n: 4, 6, 7 for n = 15, 63, 127. */
+int or_ord2(int n) {
+  int o = 1, x = 2 % n;
+  while (x != 1) { x = (2 * x) % n; o++; }
+  return o;
+}
+
+/* Generator polynomial of the narrow-sense primitive BCH code (n,k): the product of the
+ * minimal polynomials of alpha^e for odd e = 1,3,5,... (each cyclotomic coset once)
+ * until the degree reaches n-k (Sec. II, codes of Sec. IV).  g[0..n-k], g[i] = coeff
+ * of x^i.  Returns OR_ECODE if n-k is not reachable exactly. */
+int or_gen_poly(int n, int k, uint8_t *g) {
+  or_gf G;
+  if (gf_setup(&G, n) != OR_OK || k <= 0 || k >= n) return OR_EARG;
+  int used[128];
+  int poly[128];
+  memset(used, 0, sizeof(used));
+  memset(poly, 0, sizeof(poly));
+  poly[0] = 1;
+  int deg = 0;
+  for (int e = 1; deg < n - k; e += 2) {
+    if (e >= n) return OR_ECODE;
+    if (used[e]) continue;
+    int c = e;
+    do {
+      used[c] = 1;
+      int root = G.expt[c];
+      /* poly <- poly * (x + root), coefficients in GF(2^m) */
+      for (int i = deg + 1; i >= 0; i--) {
+        int hi = (i >= 1) ? poly[i - 1] : 0;
+        int lo = (i <= deg) ? gf_mul(&G, root, poly[i]) : 0;
+        poly[i] = hi ^ lo;
+      }
+      deg++;
+      c = (2 * c) % n;
+    } while (c != e);
+  }
+  if (deg != n - k) return OR_ECODE;
+  for (int i = 0; i <= deg; i++) {
+    if (poly[i] > 1) return OR_ECODE; /* a product over full cosets is binary */
+    g[i] = (uint8_t)poly[i];
+  }
+  return OR_OK;
+}
+
+/* Parity-check polynomial h(x) = (x^n + 1) / g(x), degree k, h[0..k]. */
+static int check_poly(int n, int k, uint8_t *h) {
+  uint8_t g[128], r[256];
+  int rc = or_gen_poly(n, k, g);
+  if (rc != OR_OK) return rc;
+  int dg = n - k;
+  memset(r, 0, sizeof(r));
+  r[0] = 1;
+  r[n] = 1;
+  memset(h, 0, (size_t)k + 1);
+  for (int i = n; i >= dg; i--) {
+    if (r[i]) {
+      h[i - dg] = 1;
+      for (int j = 0; j <= dg; j++) r[i - dg + j] ^= g[j];
+    }
+  }
+  for (int i = 0; i < n; i++)
+    if (r[i]) return OR_ECODE;
+  return OR_OK;
+}
+
+/* Standard cyclic parity-check matrix ((n-k) x n, one byte per entry): row r holds the
+ * reversed check polynomial starting at column r, H[r][r+i] = h[k-i], i = 0..k.  This
+ * is the banded form whose attributes Table I lists for the standard H. */
+int or_std_h(int n, int k, uint8_t *H) {
+  uint8_t h[128];
+  int rc = check_poly(n, k, h);
+  if (rc != OR_OK) return rc;
+  int M = n - k;
+  memset(H, 0, (size_t)M * n);
+  for (int r = 0; r < M; r++)
+    for (int i = 0; i <= k; i++) H[r * n + r + i] = h[k - i];
+  return OR_OK;
+}
+
+/* Systematic encoding c(x) = x^(n-k) m(x) + (x^(n-k) m(x) mod g(x)): parity bits in
+ * positions 0..n-k-1, message bit i at position n-k+i.  (The paper only states
+ * c = mG, Sec. II; this placement is the library's reading.) */
+int or_encode(int n, int k, const uint8_t *msg, int F, uint8_t *cw) {
+  uint8_t g[128];
+  int rc = or_gen_poly(n, k, g);
+  if (rc != OR_OK) return rc;
+  int dg = n - k;
+  for (int f = 0; f < F; f++) {
+    uint8_t r[128];
+    memset(r, 0, sizeof(r));
+    for (int i = 0; i < k; i++) r[dg + i] = msg[(size_t)f * k + i] & 1;
+    for (int i = n - 1; i >= dg; i--) {
+      if (r[i])
+        for (int j = 0; j <= dg; j++) r[i - dg + j] ^= g[j];
+    }
+    uint8_t *c = cw + (size_t)f * n;
+    for (int i = 0; i < dg; i++) c[i] = r[i];
+    for (int i = 0; i < k; i++) c[dg + i] = msg[(size_t)f * k + i] & 1;
+  }
+  return OR_OK;
+}
+
+/* Syndrome test H c^T = 0 (Eq. 5) for one word; returns the number of unsatisfied rows. */
+int or_syndrome_weight(const uint8_t *H, int M, int n, const uint8_t *c) {
+  int bad = 0;
+  for (int r = 0; r < M; r++) {
+    int s = 0;
+    for (int i = 0; i < n; i++) s ^= (H[r * n + i] & c[i]);
+    bad += s;
+  }
+  return bad;
+}
+
+/* Rank over GF(2) by plain Gaussian elimination on a copy. */
+int or_rank(const uint8_t *H, int M, int n) {
+  uint8_t *A = (uint8_t *)malloc((size_t)M * n + 1);
+  if (!A) return -1;
+  memcpy(A, H, (size_t)M * n);
+  int rank = 0;
+  for (int c = 0; c < n && rank < M; c++) {
+    int piv = -1;
+    for (int r = rank; r < M; r++)
+      if (A[r * n + c]) { piv = r; break; }
+    if (piv < 0) continue;
+    if (piv != rank)
+      for (int i = 0; i < n; i++) {
+        uint8_t t = A[piv * n + i];
+        A[piv * n + i] = A[rank * n + i];
+        A[rank * n + i] = t;
+      }
+    for (int r = 0; r < M; r++)
+      if (r != rank && A[r * n + c])
+        for (int i = 0; i < n; i++) A[r * n + i] ^= A[rank * n + i];
+    rank++;
+  }
+  free(A);
+  return rank;
+}
+
+/* ------------------------------------------------------------------------------
+ * BPSK / AWGN channel, Eq. (1): s = 1 - 2c, y = s + n, L = 2y / sigma^2, with
+ * sigma^2 = 1 / (2 R 10^(Eb/N0 / 10)) and R = k/n (the paper's SNR axis is Eb/N0).
+ * noise[] holds standard normal draws; the result is stored as FP32, the decoder's
+ * input format.  ebn0_db has one entry per frame.
+ * ---------------------------------------------------------------------------- */
+double or_sigma2(int n, int k, double ebn0_db) {
+  double R = (double)k / (double)n;
+  return 1.0 / (2.0 * R * pow(10.0, ebn0_db / 10.0));
+}
+
+void or_channel_llr(int n, int k, const uint8_t *cw, const double *noise, int F,
+                    const double *ebn0_db, float *llr, int ld) {
+  for (int f = 0; f < F; f++) {
+    double s2 = or_sigma2(n, k, ebn0_db[f]);
+    double sg = sqrt(s2);
+    for (int i = 0; i < n; i++) {
+      double s = 1.0 - 2.0 * (double)cw[(size_t)f * n + i];
+      double y = s + sg * noise[(size_t)f * n + i];
+      llr[(size_t)f * ld + i] = (float)(2.0 * y / s2);
+    }
+    for (int i = n; i < ld; i++) llr[(size_t)f * ld + i] = 0.0f;
+  }
+}
+
+/* ------------------------------------------------------------------------------
+ * Counter-based generators, each written from its published definition.
+ * SplitMix64: Steele, Lea & Flood, "Fast splittable pseudorandom number generators",
+ * OOPSLA 2014 (state advanced by the golden-ratio gamma, output mixed by two
+ * xor-shift-multiply steps).
+ * Philox4x32-10: Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as
+ * 1, 2, 3", SC 2011 (two 32x32->64 multiplies per round, Weyl key schedule).
+ * ---------------------------------------------------------------------------- */
+static uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* Advances *state and returns the next output. */
+uint64_t or_splitmix64(uint64_t *state) {
+  *state += 0x9E3779B97F4A7C15ULL;
+  return sm64_mix(*state);
+}
+
+/* floor(x * m / 2^64): an integer in [0, m). */
+static uint64_t draw_below(uint64_t x, uint64_t m) {
+  return (uint64_t)(((or_u128)x * (or_u128)m) >> 64);
+}
+
+static double draw_unit(uint64_t x) { return (double)(x >> 11) * (1.0 / 9007199254740992.0); }
+
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; round++) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The library's synthetic-frame recipe, restated in FP64 (see or_framegen below).
+ * A 32-bit draw w becomes the open-interval uniform ((w >> 8) + 0.5) * 2^-24, a value
+ * that is exact in both FP32 and FP64. */
+static double u24(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+/* Frame f (absolute index): key = (seed_lo, seed_hi); counter (f_lo, f_hi, b, tag).
+ *   tag 0, b 0: message bits, bit i = bit (i % 32) of word i / 32 (k <= 128).
+ *   tag 2, b 0: if ebn0_hi > ebn0_lo, Eb/N0 = lo + (hi - lo) * u24(word 0).
+ *   tag 1, b  : noise for positions 4b..4b+3 by Box-Muller on (w0,w1) and (w2,w3):
+ *               r = sqrt(-2 ln u1), z0 = r cos(2 pi u2), z1 = r sin(2 pi u2).
+ * Then systematic encoding and the channel of Eq. (1).  Outputs FP32 LLRs [F][ld],
+ * codewords [F][n] (bytes) and the per-frame Eb/N0. */
+int or_framegen(int n, int k, uint64_t seed, uint64_t frame0, int F, double ebn0_lo,
+                double ebn0_hi, float *llr, int ld, uint8_t *cw_out, double *ebn0_out) {
+  if (k > 128 || ld < n) return OR_EARG;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint8_t msg[128], cw[128];
+  for (int fi = 0; fi < F; fi++) {
+    uint64_t f = frame0 + (uint64_t)fi;
+    uint32_t ctr[4] = {(uint32_t)f, (uint32_t)(f >> 32), 0u, 0u}, w[4];
+    or_philox4x32_10(ctr, key, w);
+    for (int i = 0; i < k; i++) msg[i] = (uint8_t)((w[i / 32] >> (i % 32)) & 1u);
+    int rc = or_encode(n, k, msg, 1, cw);
+    if (rc != OR_OK) return rc;
+    double e = ebn0_lo;
+    if (ebn0_hi > ebn0_lo) {
+      uint32_t c2[4] = {(uint32_t)f, (uint32_t)(f >> 32), 0u, 2u};
+      or_philox4x32_10(c2, key, w);
+      e = ebn0_lo + (ebn0_hi - ebn0_lo) * u24(w[0]);
+    }
+    double s2 = or_sigma2(n, k, e), sg = sqrt(s2);
+    for (int b = 0; 4 * b < n; b++) {
+      uint32_t c1[4] = {(uint32_t)f, (uint32_t)(f >> 32), (uint32_t)b, 1u};
+      or_philox4x32_10(c1, key, w);
+      double z[4];
+      for (int h = 0; h < 2; h++) {
+        double u1 = u24(w[2 * h]), u2 = u24(w[2 * h + 1]);
+        double r = sqrt(-2.0 * log(u1));
+        z[2 * h] = r * cos(2.0 * M_PI * u2);
+        z[2 * h + 1] = r * sin(2.0 * M_PI * u2);
+      }
+      for (int h = 0; h < 4 && 4 * b + h < n; h++) {
+        int i = 4 * b + h;
+        double y = (1.0 - 2.0 * (double)cw[i]) + sg * z[h];
+        llr[(size_t)fi * ld + i] = (float)(2.0 * y / s2);
+      }
+    }
+    for (int i = n; i < ld; i++) llr[(size_t)fi * ld + i] = 0.0f;
+    if (cw_out) memcpy(cw_out + (size_t)fi * n, cw, (size_t)n);
+    if (ebn0_out) ebn0_out[fi] = e;
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------
+ * Automorphisms (Sec. III-B).  Each frame gets P pairs (s, j) acting as
+ * pi(i) = (2^j i + s) mod n: a Frobenius map i -> 2i applied j times followed by a
+ * cyclic shift by s.  Draw for frame f, slot p, attempt a:
+ *   x = splitmix64 output number 1 + (f P + p) 16 + a from state `seed`
+ *   s = floor((x mod 2^32) n / 2^32),  j = floor((x >> 32) ord / 2^32)
+ * retried (a = 1..15) while (s, j) repeats an earlier slot of the same frame; after
+ * 16 attempts the last draw stands.  Packed as s | j << 8.
+ * ---------------------------------------------------------------------------- */
+int or_draw_autos(int n, int P, uint64_t seed, uint64_t frame0, int F, uint16_t *out) {
+  if (n != 15 && n != 63 && n != 127) return OR_EARG;
+  int ord = or_ord2(n);
+  for (int fi = 0; fi < F; fi++) {
+    uint64_t f = frame0 + (uint64_t)fi;
+    for (int p = 0; p < P; p++) {
+      int s = 0, j = 0;
+      for (int a = 0; a < 16; a++) {
+        uint64_t cnt = 1 + (f * (uint64_t)P + (uint64_t)p) * 16 + (uint64_t)a;
+        uint64_t x = sm64_mix(seed + 0x9E3779B97F4A7C15ULL * cnt);
+        s = (int)(((x & 0xffffffffULL) * (uint64_t)n) >> 32);
+        j = (int)(((x >> 32) * (uint64_t)ord) >> 32);
+        int clash = 0;
+        for (int q = 0; q < p; q++) {
+          uint16_t v = out[(size_t)fi * P + q];
+          if ((v & 0xff) == s && (v >> 8) == j) clash = 1;
+        }
+        if (!clash) break;
+      }
+      out[(size_t)fi * P + p] = (uint16_t)(s | (j << 8));
+    }
+  }
+  return OR_OK;
+}
+
+/* pi(i) = (2^j i + s) mod n for a packed pair. */
+static int auto_apply(uint16_t v, int n, int i) {
+  int s = v & 0xff, j = v >> 8;
+  long long t = i;
+  for (int q = 0; q < j; q++) t = (2 * t) % n;
+  return (int)((t + s) % n);
+}
+
+/* ------------------------------------------------------------------------------
+ * Optimized parity-check matrix H_o (Sec. III-A, steps 1-6), one byte per entry.
+ * ---------------------------------------------------------------------------- */
+static int row_weight(const uint8_t *r, int n) {
+  int w = 0;
+  for (int i = 0; i < n; i++) w += r[i];
+  return w;
+}
+
+/* rot(r, q)[i] = r[(i - q) mod n]: multiplication of r(x) by x^q modulo x^n - 1. */
+static void row_rot(const uint8_t *r, int n, int q, uint8_t *out) {
+  for (int i = 0; i < n; i++) out[(i + q) % n] = r[i];
+}
+
+/* Lexicographically smallest rotation (byte string order) -- a canonical member of the
+ * cyclic class, used only to test "is a cyclic shift of an existing row". */
+static void row_canon(const uint8_t *r, int n, uint8_t *out) {
+  uint8_t tmp[128];
+  memcpy(out, r, (size_t)n);
+  for (int q = 1; q < n; q++) {
+    row_rot(r, n, q, tmp);
+    if (memcmp(tmp, out, (size_t)n) < 0) memcpy(out, tmp, (size_t)n);
+  }
+}
+
+typedef struct {
+  int n, cap, len;
+  uint8_t *rows;  /* len x n */
+  uint8_t *canon; /* len x n */
+} rowlist;
+
+static int rl_push(rowlist *L, const uint8_t *r) {
+  if (L->len == L->cap) {
+    int nc = L->cap ? 2 * L->cap : 64;
+    uint8_t *a = (uint8_t *)realloc(L->rows, (size_t)nc * L->n);
+    if (!a) return OR_ENOMEM;
+    L->rows = a;
+    uint8_t *b = (uint8_t *)realloc(L->canon, (size_t)nc * L->n);
+    if (!b) return OR_ENOMEM;
+    L->canon = b;
+    L->cap = nc;
+  }
+  memcpy(L->rows + (size_t)L->len * L->n, r, (size_t)L->n);
+  row_canon(r, L->n, L->canon + (size_t)L->len * L->n);
+  L->len++;
+  return OR_OK;
+}
+
+static int rl_has_class(const rowlist *L, const uint8_t *r) {
+  uint8_t c[128];
+  row_canon(r, L->n, c);
+  for (int i = 0; i < L->len; i++)
+    if (memcmp(L->canon + (size_t)i * L->n, c, (size_t)L->n) == 0) return 1;
+  return 0;
+}
+
+static void rl_free(rowlist *L) {
+  free(L->rows);
+  free(L->canon);
+  L->rows = L->canon = NULL;
+  L->len = L->cap = 0;
+}
+
+/* Step 3 (and, with shifts, one round of step 4): for each row r_i, collect in S_f the
+ * lightest nonzero words r_i xor r_j (j != i; with shifts, r_j replaced by each
+ * rotation r_j^(q), q = 1..n), keeping r_i itself unless something lighter appears;
+ * append S_f to S_g, skipping any word that is a cyclic shift of a word already in S_g
+ * (the first orientation met is kept).  Returns S_g in insertion order. */
+static int row_sum_pass(const rowlist *in, int with_shifts, rowlist *out) {
+  int n = in->n, m = in->len;
+  uint8_t t[128], rj[128];
+  uint8_t *Sf = (uint8_t *)malloc((size_t)n * 4096);
+  int sf_cap = 4096;
+  if (!Sf) return OR_ENOMEM;
+  out->n = n;
+  for (int i = 0; i < m; i++) {
+    const uint8_t *ri = in->rows + (size_t)i * n;
+    int wg = row_weight(ri, n);
+    int nf = 1;
+    memcpy(Sf, ri, (size_t)n);
+    for (int j = 0; j < m; j++) {
+      if (j == i) continue;
+      int nq = with_shifts ? n : 1;
+      for (int qq = 1; qq <= nq; qq++) {
+        int q = with_shifts ? (qq % n) : 0;
+        row_rot(in->rows + (size_t)j * n, n, q, rj);
+        for (int x = 0; x < n; x++) t[x] = ri[x] ^ rj[x];
+        int w = row_weight(t, n);
+        if (w == 0) continue;
+        if (w == wg) {
+          if (nf == sf_cap) {
+            uint8_t *a = (uint8_t *)realloc(Sf, (size_t)n * sf_cap * 2);
+            if (!a) { free(Sf); return OR_ENOMEM; }
+            Sf = a;
+            sf_cap *= 2;
+          }
+          memcpy(Sf + (size_t)nf * n, t, (size_t)n);
+          nf++;
+        } else if (w < wg) {
+          wg = w;
+          nf = 1;
+          memcpy(Sf, t, (size_t)n);
+        }
+      }
+    }
+    for (int a = 0; a < nf; a++) {
+      const uint8_t *cand = Sf + (size_t)a * n;
+      if (!rl_has_class(out, cand)) {
+        int rc = rl_push(out, cand);
+        if (rc != OR_OK) { free(Sf); return rc; }
+      }
+    }
+  }
+  free(Sf);
+  return OR_OK;
+}
+
+/* Keep the `cap` lightest rows of L, stable by weight (insertion order among equals). */
+static int truncate_lightest(rowlist *L, int cap) {
+  if (L->len <= cap) return OR_OK;
+  int n = L->n;
+  rowlist out = {n, 0, 0, NULL, NULL};
+  int maxw = n;
+  for (int w = 0; w <= maxw && out.len < cap; w++)
+    for (int i = 0; i < L->len && out.len < cap; i++) {
+      const uint8_t *r = L->rows + (size_t)i * n;
+      if (row_weight(r, n) == w) {
+        int rc = rl_push(&out, r);
+        if (rc != OR_OK) { rl_free(&out); return rc; }
+      }
+    }
+  rl_free(L);
+  *L = out;
+  return OR_OK;
+}
+
+static long long c2(long long x) { return x * (x - 1) / 2; }
+
+static int overlap(const uint8_t *a, const uint8_t *b, int n) {
+  int o = 0;
+  for (int i = 0; i < n; i++) o += a[i] & b[i];
+  return o;
+}
+
+static int find_row(const uint8_t *rows, int M, int n, const uint8_t *r, int skip) {
+  for (int i = 0; i < M; i++)
+    if (i != skip && memcmp(rows + (size_t)i * n, r, (size_t)n) == 0) return i;
+  return -1;
+}
+
+/* Build H_o (m_rows x n; m_rows <= 0 selects 2(n-k), clamped to the distinct rows
+ * reachable; Ho must hold 2(n-k) x n bytes in that case).  Readings of the under-specified steps (all deterministic):
+ *  step 2  reduced row echelon form, pivots by ascending column, rows by pivot column;
+ *  step 3  as row_sum_pass without shifts;
+ *  step 4  q_rounds rounds of row_sum_pass with shifts, each on the lightest
+ *          2 m_rows rows (stable) of the previous result;
+ *  step 5  rows sorted by ascending weight (stable); if there are at least m_rows of
+ *          them the lightest m_rows are kept, otherwise copies are appended cycling
+ *          through the sorted list, each rotated by q = draw_below(n) (redrawn up to
+ *          4n times while the rotation duplicates a row already present);
+ *  step 6  simulated annealing: sa_steps proposals; each draws (in this order) a row r
+ *          with probability (cycles4(r) + 1) / sum, a shift q in [1, n-1] and a
+ *          uniform u.  Loss = C4 + lambda Var_pop(column weights), so
+ *          Delta = dC4 + lambda dSumSq / n; a proposal duplicating another row is
+ *          rejected, otherwise accepted if Delta <= 0 or u < exp(-Delta / T); T starts
+ *          at t0_frac * loss_0 and is multiplied by cool after every proposal;
+ *  repair  if rank < n-k, rows in order try rotations q = 1..n-1 and keep the first
+ *          that raises the rank, until rank = n-k; else OR_ERANK.
+ * The PRNG is SplitMix64 with state `seed`, consumed in exactly that order. */
+int or_build_ho(int n, int k, int m_rows, uint64_t seed, int q_rounds, int sa_steps,
+                double sa_lambda, double sa_t0_frac, double sa_cool, uint8_t *Ho,
+                int *r1_count, int *m_rows_out) {
+  int M = n - k;
+  int want_default = m_rows <= 0;
+  if (want_default) m_rows = 2 * M;
+  if (m_rows < M) return OR_EARG;
+  uint8_t *Hs = (uint8_t *)malloc((size_t)M * n);
+  if (!Hs) return OR_ENOMEM;
+  int rc = or_std_h(n, k, Hs);
+  if (rc != OR_OK) { free(Hs); return rc; }
+
+  /* step 2: reduced row echelon form */
+  int rank = 0;
+  for (int c = 0; c < n && rank < M; c++) {
+    int piv = -1;
+    for (int r = rank; r < M; r++)
+      if (Hs[r * n + c]) { piv = r; break; }
+    if (piv < 0) continue;
+    if (piv != rank)
+      for (int i = 0; i < n; i++) {
+        uint8_t t = Hs[piv * n + i];
+        Hs[piv * n + i] = Hs[rank * n + i];
+        Hs[rank * n + i] = t;
+      }
+    for (int r = 0; r < M; r++)
+      if (r != rank && Hs[r * n + c])
+        for (int i = 0; i < n; i++) Hs[r * n + i] ^= Hs[rank * n + i];
+    rank++;
+  }
+
+  rowlist cur = {n, 0, 0, NULL, NULL};
+  for (int r = 0; r < M; r++) {
+    rc = rl_push(&cur, Hs + (size_t)r * n);
+    if (rc != OR_OK) { free(Hs); rl_free(&cur); return rc; }
+  }
+  free(Hs);
+
+  /* step 3 */
+  rowlist nxt = {n, 0, 0, NULL, NULL};
+  rc = row_sum_pass(&cur, 0, &nxt);
+  rl_free(&cur);
+  if (rc != OR_OK) { rl_free(&nxt); return rc; }
+  cur = nxt;
+  /* step 4: each round works on the lightest 2 m_rows rows of the previous result
+   * (stable by weight) -- only the lightest rows are ever kept, and equal-weight ties
+   * would otherwise make the list grow round after round */
+  for (int q = 0; q < q_rounds; q++) {
+    rowlist o2 = {n, 0, 0, NULL, NULL};
+    rc = truncate_lightest(&cur, 2 * m_rows);
+    if (rc != OR_OK) { rl_free(&cur); return rc; }
+    rc = row_sum_pass(&cur, 1, &o2);
+    rl_free(&cur);
+    if (rc != OR_OK) { rl_free(&o2); return rc; }
+    cur = o2;
+  }
+  if (r1_count) *r1_count = cur.len;
+  /* Distinct rows available: the sum of the cyclic-class sizes of H_r1.  The default
+   * row count 2(n-k) is clamped to it (BCH(15,7) has a single weight-4 class of 15
+   * rows); an explicit request beyond it is an argument error. */
+  {
+    long long avail = 0;
+    uint8_t tr[128];
+    for (int i = 0; i < cur.len; i++) {
+      const uint8_t *r = cur.rows + (size_t)i * n;
+      int per = n;
+      for (int q = 1; q < n; q++) {
+        row_rot(r, n, q, tr);
+        if (memcmp(tr, r, (size_t)n) == 0) { per = q; break; }
+      }
+      avail += per;
+    }
+    if (want_default && m_rows > avail) m_rows = (int)avail;
+    if (m_rows > avail || m_rows < M) { rl_free(&cur); return OR_EARG; }
+    if (m_rows_out) *m_rows_out = m_rows;
+  }
+
+  /* step 5: stable sort by weight (insertion sort on an index array) */
+  int L = cur.len;
+  int *ord = (int *)malloc(sizeof(int) * (size_t)(L > 0 ? L : 1));
+  if (!ord) { rl_free(&cur); return OR_ENOMEM; }
+  for (int i = 0; i < L; i++) ord[i] = i;
+  for (int i = 1; i < L; i++) {
+    int v = ord[i], wv = row_weight(cur.rows + (size_t)v * n, n);
+    int j = i - 1;
+    while (j >= 0 && row_weight(cur.rows + (size_t)ord[j] * n, n) > wv) {
+      ord[j + 1] = ord[j];
+      j--;
+    }
+    ord[j + 1] = v;
+  }
+  uint64_t st = seed;
+  int have = 0;
+  uint8_t *H = Ho;
+  memset(H, 0, (size_t)m_rows * n);
+  for (int i = 0; i < L && have < m_rows; i++) {
+    memcpy(H + (size_t)have * n, cur.rows + (size_t)ord[i] * n, (size_t)n);
+    have++;
+  }
+  uint8_t cand[128];
+  int c = 0;
+  while (have < m_rows) {
+    if (L == 0 || c > 8 * m_rows + 8 * L) { free(ord); rl_free(&cur); return OR_ERANK; }
+    const uint8_t *src = cur.rows + (size_t)ord[c % L] * n;
+    c++;
+    for (int a = 0; a < 4 * n; a++) {
+      int q = (int)draw_below(or_splitmix64(&st), (uint64_t)n);
+      row_rot(src, n, q, cand);
+      if (find_row(H, have, n, cand, -1) < 0) {
+        memcpy(H + (size_t)have * n, cand, (size_t)n);
+        have++;
+        break;
+      }
+    }
+  }
+  free(ord);
+  rl_free(&cur);
+
+  /* step 6: simulated annealing over cyclic row shifts */
+  int Mo = m_rows;
+  long long *ov = (long long *)malloc(sizeof(long long) * (size_t)Mo * Mo);
+  long long *cyc = (long long *)malloc(sizeof(long long) * (size_t)Mo);
+  long long *nov = (long long *)malloc(sizeof(long long) * (size_t)Mo);
+  long long colw[128];
+  if (!ov || !cyc || !nov) { free(ov); free(cyc); free(nov); return OR_ENOMEM; }
+  memset(colw, 0, sizeof(colw));
+  long long E = 0;
+  for (int r = 0; r < Mo; r++)
+    for (int i = 0; i < n; i++) { colw[i] += H[(size_t)r * n + i]; E += H[(size_t)r * n + i]; }
+  long long C4 = 0;
+  for (int r = 0; r < Mo; r++) {
+    cyc[r] = 0;
+    for (int r2 = 0; r2 < Mo; r2++) {
+      ov[(size_t)r * Mo + r2] = (r == r2) ? 0 : overlap(H + (size_t)r * n, H + (size_t)r2 * n, n);
+    }
+  }
+  for (int r = 0; r < Mo; r++)
+    for (int r2 = 0; r2 < Mo; r2++)
+      if (r2 != r) cyc[r] += c2(ov[(size_t)r * Mo + r2]);
+  for (int r = 0; r < Mo; r++)
+    for (int r2 = r + 1; r2 < Mo; r2++) C4 += c2(ov[(size_t)r * Mo + r2]);
+  long long SS = 0;
+  for (int i = 0; i < n; i++) SS += colw[i] * colw[i];
+  double loss0 = (double)C4 + sa_lambda * ((double)SS - (double)E * (double)E / (double)n) / (double)n;
+  double T = sa_t0_frac * loss0;
+  uint8_t nr[128];
+  for (int s = 0; s < sa_steps; s++) {
+    uint64_t x1 = or_splitmix64(&st);
+    uint64_t x2 = or_splitmix64(&st);
+    uint64_t x3 = or_splitmix64(&st);
+    long long W = 0;
+    for (int r = 0; r < Mo; r++) W += cyc[r] + 1;
+    long long tsel = (long long)draw_below(x1, (uint64_t)W);
+    int r = 0;
+    long long acc = 0;
+    for (r = 0; r < Mo; r++) {
+      acc += cyc[r] + 1;
+      if (acc > tsel) break;
+    }
+    int q = 1 + (int)draw_below(x2, (uint64_t)(n - 1));
+    double u = draw_unit(x3);
+    const uint8_t *old = H + (size_t)r * n;
+    row_rot(old, n, q, nr);
+    int accept = 0;
+    if (find_row(H, Mo, n, nr, r) < 0) {
+      long long dC4 = 0;
+      for (int r2 = 0; r2 < Mo; r2++) {
+        if (r2 == r) { nov[r2] = 0; continue; }
+        nov[r2] = overlap(nr, H + (size_t)r2 * n, n);
+        dC4 += c2(nov[r2]) - c2(ov[(size_t)r * Mo + r2]);
+      }
+      long long dSS = 0;
+      for (int i = 0; i < n; i++) {
+        long long w1 = colw[i] - old[i] + nr[i];
+        dSS += w1 * w1 - colw[i] * colw[i];
+      }
+      double d = (double)dC4 + sa_lambda * (double)dSS / (double)n;
+      if (d <= 0.0) accept = 1;
+      else if (T > 0.0 && u < exp(-d / T)) accept = 1;
+      if (accept) {
+        for (int i = 0; i < n; i++) colw[i] += (long long)nr[i] - (long long)old[i];
+        for (int r2 = 0; r2 < Mo; r2++) {
+          if (r2 == r) continue;
+          long long o = ov[(size_t)r * Mo + r2];
+          cyc[r2] += c2(nov[r2]) - c2(o);
+          ov[(size_t)r * Mo + r2] = nov[r2];
+          ov[(size_t)r2 * Mo + r] = nov[r2];
+        }
+        cyc[r] = 0;
+        for (int r2 = 0; r2 < Mo; r2++)
+          if (r2 != r) cyc[r] += c2(ov[(size_t)r * Mo + r2]);
+        C4 += dC4;
+        memcpy(H + (size_t)r * n, nr, (size_t)n);
+      }
+    }
+    T *= sa_cool;
+  }
+  free(ov);
+  free(cyc);
+  free(nov);
+
+  /* rank repair */
+  int rk = or_rank(H, Mo, n);
+  uint8_t *tmp = (uint8_t *)malloc((size_t)Mo * n);
+  if (!tmp) return OR_ENOMEM;
+  for (int r = 0; r < Mo && rk < M; r++) {
+    for (int q = 1; q < n; q++) {
+      row_rot(H + (size_t)r * n, n, q, nr);
+      if (find_row(H, Mo, n, nr, r) >= 0) continue;
+      memcpy(tmp, H, (size_t)Mo * n);
+      memcpy(tmp + (size_t)r * n, nr, (size_t)n);
+      int r2 = or_rank(tmp, Mo, n);
+      if (r2 > rk) {
+        memcpy(H + (size_t)r * n, nr, (size_t)n);
+        rk = r2;
+        break;
+      }
+    }
+  }
+  free(tmp);
+  if (rk != M) return OR_ERANK;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------
+ * Min-sum check-to-variable message of Eq. (3) for one edge, written literally: the
+ * product of the signs and the minimum magnitude over all OTHER variables of the row.
+ * sgn(0) = +1.
+ * ---------------------------------------------------------------------------- */
+static double c2v_literal(const double *v2c_row, const int *vars, int w, int self, double alpha) {
+  double sg = 1.0, mn = INFINITY;
+  for (int e = 0; e < w; e++) {
+    if (e == self) continue;
+    double x = v2c_row[e];
+    if (x < 0.0) sg = -sg;
+    double a = fabs(x);
+    if (a < mn) mn = a;
+  }
+  (void)vars;
+  return alpha * sg * mn;
+}
+
+static int row_vars(const uint8_t *H, int n, int r, int *vars) {
+  int w = 0;
+  for (int i = 0; i < n; i++)
+    if (H[r * n + i]) vars[w++] = i;
+  return w;
+}
+
+/* Plain flooding NMS, Eqs. (2)-(5).  c2v^(0) = 0; v2c^(t) = L + sum of the OTHER
+ * incoming c2v^(t-1); c2v^(t) by Eq. (3); the output x^(t) = L + sum of ALL c2v^(t)
+ * (Eq. 4 read with the latest messages, otherwise iteration 1 could never change a
+ * decision); hard decision c_i = [x_i < 0]; stop when H c^T = 0 (if early_stop) or
+ * after `iters` iterations.  Outputs per frame: hard bits (bytes), iterations run,
+ * converged flag, final x (double). */
+int or_nms_plain(const uint8_t *H, int M, int n, const float *llr, int ld, int F, int iters,
+                 double alpha, int early_stop, uint8_t *hard, int *iters_used,
+                 uint8_t *converged, double *y_out) {
+  double *c2v = (double *)calloc((size_t)M * n, sizeof(double));
+  double *nc2v = (double *)calloc((size_t)M * n, sizeof(double));
+  double *v2c = (double *)calloc((size_t)M * n, sizeof(double));
+  int *vars = (int *)malloc(sizeof(int) * (size_t)n);
+  double x[128], rowbuf[128];
+  uint8_t c[128];
+  if (!c2v || !nc2v || !v2c || !vars) { free(c2v); free(nc2v); free(v2c); free(vars); return OR_ENOMEM; }
+  for (int f = 0; f < F; f++) {
+    const float *L = llr + (size_t)f * ld;
+    memset(c2v, 0, sizeof(double) * (size_t)M * n);
+    int t_run = 0, ok = 0;
+    for (int i = 0; i < n; i++) {
+      x[i] = (double)L[i];
+      c[i] = x[i] < 0.0;
+    }
+    for (int t = 1; t <= iters; t++) {
+      /* Eq. (2) */
+      for (int j = 0; j < M; j++)
+        for (int i = 0; i < n; i++) {
+          if (!H[j * n + i]) continue;
+          double s = (double)L[i];
+          for (int kk = 0; kk < M; kk++)
+            if (kk != j && H[kk * n + i]) s += c2v[kk * n + i];
+          v2c[j * n + i] = s;
+        }
+      /* Eq. (3) */
+      for (int j = 0; j < M; j++) {
+        int w = row_vars(H, n, j, vars);
+        for (int e = 0; e < w; e++) rowbuf[e] = v2c[j * n + vars[e]];
+        for (int e = 0; e < w; e++) nc2v[j * n + vars[e]] = c2v_literal(rowbuf, vars, w, e, alpha);
+      }
+      memcpy(c2v, nc2v, sizeof(double) * (size_t)M * n);
+      /* Eq. (4) */
+      for (int i = 0; i < n; i++) {
+        double s = (double)L[i];
+        for (int j = 0; j < M; j++)
+          if (H[j * n + i]) s += c2v[j * n + i];
+        x[i] = s;
+        c[i] = s < 0.0;
+      }
+      t_run = t;
+      ok = or_syndrome_weight(H, M, n, c) == 0;
+      if (early_stop && ok) break;
+    }
+    if (hard) memcpy(hard + (size_t)f * n, c, (size_t)n);
+    if (iters_used) iters_used[f] = t_run;
+    if (converged) converged[f] = (uint8_t)ok;
+    if (y_out) memcpy(y_out + (size_t)f * n, x, sizeof(double) * (size_t)n);
+  }
+  free(c2v); free(nc2v); free(v2c); free(vars);
+  return OR_OK;
+}
+
+/* One iteration of the enhanced decoder (Algorithm 1, steps 2-4), reading A:
+ *   z_p[pi_p(i)] = y[i]                       dilation into the block B(y)
+ *   v2c = z_p on every edge                   Eq. (2) with c2v^(0) = 0
+ *   c2v_p(j,u) by Eq. (3) with alpha_t
+ *   S_p[u] = sum over rows j containing u of c2v_p(j,u)
+ *   y_new[i] = y[i] + (S_1[pi_1(i)] + ... + S_P[pi_P(i)]) / P    un-permute, average,
+ *                                                               then Eq. (4)
+ * Also returns the smallest |v2c| seen (a sign-decision margin). */
+static double enhanced_iteration(const uint8_t *Ho, int M, int n, int P, const uint16_t *aut,
+                                 double alpha_t, const double *y, double *y_new,
+                                 double *mag_out) {
+  double z[128], S[128], sum[128], mag[128], rowbuf[128];
+  int vars[128];
+  double margin = INFINITY;
+  for (int i = 0; i < n; i++) { sum[i] = 0.0; mag[i] = 0.0; }
+  for (int p = 0; p < P; p++) {
+    int pi[128];
+    for (int i = 0; i < n; i++) {
+      pi[i] = auto_apply(aut[p], n, i);
+      z[pi[i]] = y[i];
+    }
+    double Sa[128];
+    for (int u = 0; u < n; u++) { S[u] = 0.0; Sa[u] = 0.0; }
+    for (int j = 0; j < M; j++) {
+      int w = row_vars(Ho, n, j, vars);
+      for (int e = 0; e < w; e++) {
+        rowbuf[e] = z[vars[e]];
+        if (fabs(rowbuf[e]) < margin) margin = fabs(rowbuf[e]);
+      }
+      for (int e = 0; e < w; e++) {
+        double m = c2v_literal(rowbuf, vars, w, e, alpha_t);
+        S[vars[e]] += m;
+        Sa[vars[e]] += fabs(m);
+      }
+    }
+    for (int i = 0; i < n; i++) {
+      sum[i] += S[pi[i]];
+      mag[i] += Sa[pi[i]];
+    }
+  }
+  for (int i = 0; i < n; i++) {
+    y_new[i] = y[i] + sum[i] / (double)P;
+    if (mag_out) mag_out[i] = fabs(y[i]) + mag[i] / (double)P;
+  }
+  return margin;
+}
+
+/* Enhanced NMS decoder, Algorithm 1 (reading A: the only state carried between
+ * iterations is y; each iteration dilates the current y afresh).  autos: [F][P]
+ * packed pairs; alpha: per-iteration factors alpha_1..alpha_iters.  The early-stop
+ * test is H_o c^T = 0 (Algorithm 1, step 5).  Optional outputs:
+ *   y_out     [F][n]           final y^(t)
+ *   trace     [F][iters+1][n]  y^(0..t) (entries past the stop repeat the last y)
+ *   mag       [F][iters][n]    |y^(t-1)_i| + mean_p sum_j |c2v| (operand magnitude)
+ *   margin    [F]              smallest |v2c| or |y^(t)| met while decoding. */
+int or_nms_enhanced(const uint8_t *Ho, int M, int n, const float *llr, int ld, int F, int P,
+                    const uint16_t *autos, int iters, const double *alpha, int early_stop,
+                    uint8_t *hard, int *iters_used, uint8_t *converged, double *y_out,
+                    double *trace, double *mag, double *margin) {
+  double y[128], yn[128], mg[128];
+  uint8_t c[128];
+  for (int f = 0; f < F; f++) {
+    const float *L = llr + (size_t)f * ld;
+    double mar = INFINITY;
+    for (int i = 0; i < n; i++) {
+      y[i] = (double)L[i];
+      c[i] = y[i] < 0.0;
+      if (fabs(y[i]) < mar) mar = fabs(y[i]);
+    }
+    if (trace) memcpy(trace + (size_t)f * (iters + 1) * n, y, sizeof(double) * (size_t)n);
+    int t_run = 0, ok = 0;
+    for (int t = 1; t <= iters; t++) {
+      double m = enhanced_iteration(Ho, M, n, P, autos + (size_t)f * P, alpha[t - 1], y, yn, mg);
+      if (m < mar) mar = m;
+      for (int i = 0; i < n; i++) {
+        c[i] = yn[i] < 0.0;
+        if (fabs(yn[i]) < mar) mar = fabs(yn[i]);
+      }
+      if (mag) memcpy(mag + ((size_t)f * iters + (size_t)(t - 1)) * n, mg, sizeof(double) * (size_t)n);
+      memcpy(y, yn, sizeof(double) * (size_t)n);
+      if (trace) memcpy(trace + ((size_t)f * (iters + 1) + (size_t)t) * n, y, sizeof(double) * (size_t)n);
+      t_run = t;
+      ok = or_syndrome_weight(Ho, M, n, c) == 0;
+      if (early_stop && ok) break;
+    }
+    if (trace)
+      for (int t = t_run + 1; t <= iters; t++)
+        memcpy(trace + ((size_t)f * (iters + 1) + (size_t)t) * n, y, sizeof(double) * (size_t)n);
+    if (hard) memcpy(hard + (size_t)f * n, c, (size_t)n);
+    if (iters_used) iters_used[f] = t_run;
+    if (converged) converged[f] = (uint8_t)ok;
+    if (y_out) memcpy(y_out + (size_t)f * n, y, sizeof(double) * (size_t)n);
+    if (margin) margin[f] = mar;
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------
+ * Order-p ordered-statistics decoding (Sec. II-B) on the standard H (full rank).
+ *  1. reliability |L_i| of the FP32 channel LLR; positions sorted ascending
+ *     (stable: equal values keep index order);
+ *  2. the columns of H taken in that order; Gaussian elimination pivots, column by
+ *     column, on the lowest not-yet-pivoted row holding a 1, clearing that column in
+ *     every other row; the n-k pivot columns are the least reliable independent
+ *     positions and the remaining k columns form the most reliable basis (MRB);
+ *  3. candidates: MRB bits = hard(L) xor e with wt(e) <= p, enumerated weight 0, then
+ *     weight 1 by MRB position in sorted order, then weight 2 in lexicographic order
+ *     (order p > 2 continues lexicographically by weight); each pivot bit is solved
+ *     from its reduced row;
+ *  4. likelihood: the candidate minimising sum over disagreeing positions of
+ *     w_i = floor(|L_i| 2^24) (clipped at 2^40, integer so the sum is exact) -- for
+ *     BPSK/AWGN this is the highest-likelihood candidate; ties keep the first.
+ * Output: codeword bytes [F][n] and its score. */
+static int next_comb(int *idx, int w, int K) {
+  int i = w - 1;
+  while (i >= 0 && idx[i] == K - w + i) i--;
+  if (i < 0) return 0;
+  idx[i]++;
+  for (int j = i + 1; j < w; j++) idx[j] = idx[j - 1] + 1;
+  return 1;
+}
+
+int or_osd(const uint8_t *H, int M, int n, const float *llr, int ld, int F, int order,
+           uint8_t *cw_out, uint64_t *score_out, int *mrb_out) {
+  uint8_t *A = (uint8_t *)malloc((size_t)M * n);
+  if (!A) return OR_ENOMEM;
+  for (int f = 0; f < F; f++) {
+    const float *L = llr + (size_t)f * ld;
+    uint64_t w[128];
+    uint8_t hard[128];
+    int perm[128];
+    for (int i = 0; i < n; i++) {
+      double a = fabs((double)L[i]) * 16777216.0;
+      double fl = floor(a);
+      if (fl > 1099511627776.0) fl = 1099511627776.0;
+      w[i] = (uint64_t)fl;
+      hard[i] = L[i] < 0.0f;
+      perm[i] = i;
+    }
+    /* stable insertion sort by |L| ascending */
+    for (int i = 1; i < n; i++) {
+      int v = perm[i];
+      float av = fabsf(L[v]);
+      int j = i - 1;
+      while (j >= 0 && fabsf(L[perm[j]]) > av) { perm[j + 1] = perm[j]; j--; }
+      perm[j + 1] = v;
+    }
+    for (int r = 0; r < M; r++)
+      for (int q = 0; q < n; q++) A[r * n + q] = H[r * n + perm[q]];
+    int pivcol[128], is_piv[128], used[128];
+    memset(is_piv, 0, sizeof(is_piv));
+    memset(used, 0, sizeof(used));
+    int np = 0;
+    for (int q = 0; q < n && np < M; q++) {
+      int pr = -1;
+      for (int r = 0; r < M; r++)
+        if (!used[r] && A[r * n + q]) { pr = r; break; }
+      if (pr < 0) continue;
+      used[pr] = 1;
+      pivcol[pr] = q;
+      is_piv[q] = 1;
+      for (int r = 0; r < M; r++)
+        if (r != pr && A[r * n + q])
+          for (int x = 0; x < n; x++) A[r * n + x] ^= A[pr * n + x];
+      np++;
+    }
+    if (np != M) { free(A); return OR_ERANK; }
+    int mrb[128], K = 0;
+    for (int q = 0; q < n; q++)
+      if (!is_piv[q]) mrb[K++] = q;
+    if (mrb_out)
+      for (int a = 0; a < K; a++) mrb_out[(size_t)f * K + a] = perm[mrb[a]];
+    uint8_t best[128], cand[128];
+    uint64_t best_s = UINT64_MAX;
+    for (int wt = 0; wt <= order && wt <= K; wt++) {
+      int idx[128];
+      for (int a = 0; a < wt; a++) idx[a] = a;
+      do {
+        for (int a = 0; a < K; a++) cand[mrb[a]] = hard[perm[mrb[a]]];
+        for (int a = 0; a < wt; a++) cand[mrb[idx[a]]] ^= 1;
+        for (int r = 0; r < M; r++) {
+          int s = 0;
+          for (int a = 0; a < K; a++) s ^= A[r * n + mrb[a]] & cand[mrb[a]];
+          cand[pivcol[r]] = (uint8_t)s;
+        }
+        uint64_t sc = 0;
+        for (int q = 0; q < n; q++)
+          if (cand[q] != hard[perm[q]]) sc += w[perm[q]];
+        if (sc < best_s) {
+          best_s = sc;
+          for (int q = 0; q < n; q++) best[perm[q]] = cand[q];
+        }
+      } while (wt > 0 && next_comb(idx, wt, K));
+    }
+    memcpy(cw_out + (size_t)f * n, best, (size_t)n);
+    if (score_out) score_out[f] = best_s;
+  }
+  free(A);
+  return OR_OK;
+}
+
+/* Exhaustive maximum-likelihood decoding over all 2^k codewords (small codes only):
+ * argmax of sum_i (1 - 2 c_i) L_i; ties keep the lowest message index
+ * (message integer = sum m_i 2^i). */
+int or_ml(int n, int k, const float *llr, int ld, int F, uint8_t *cw_out) {
+  if (k > 20) return OR_EARG;
+  int ncw = 1 << k;
+  uint8_t *book = (uint8_t *)malloc((size_t)ncw * n);
+  uint8_t *msg = (uint8_t *)malloc((size_t)ncw * k);
+  if (!book || !msg) { free(book); free(msg); return OR_ENOMEM; }
+  for (int m = 0; m < ncw; m++)
+    for (int i = 0; i < k; i++) msg[(size_t)m * k + i] = (uint8_t)((m >> i) & 1);
+  int rc = or_encode(n, k, msg, ncw, book);
+  if (rc != OR_OK) { free(book); free(msg); return rc; }
+  for (int f = 0; f < F; f++) {
+    const float *L = llr + (size_t)f * ld;
+    double best = -INFINITY;
+    int bi = 0;
+    for (int m = 0; m < ncw; m++) {
+      double s = 0.0;
+      for (int i = 0; i < n; i++) s += (1.0 - 2.0 * book[(size_t)m * n + i]) * (double)L[i];
+      if (s > best) { best = s; bi = m; }
+    }
+    memcpy(cw_out + (size_t)f * n, book + (size_t)bi * n, (size_t)n);
+  }
+  free(book);
+  free(msg);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------
+ * Training pass of the enhanced decoder with per-iteration factors alpha_t (the
+ * paper tunes alpha by treating NMS as a neural network, Sec. II-A and Sec. IV):
+ * all `iters` iterations (no early stop), loss = mean over frames and bits of
+ * softplus(-(1 - 2 c_i) y_i) on the final y (binary cross-entropy with
+ * P(c_i = 1) = sigmoid(-y_i)), and its subgradient:
+ *   d c2v(j,u) / d alpha_t = c2v(j,u) / alpha_t
+ *   d c2v(j,u) / d z_a     = alpha_t * prod_{u' != u} sgn z_u' * sgn z_a, where a is
+ *                            the position of the minimum over the row without u
+ *                            (lowest column on ties); sign derivatives are zero;
+ *   the dilation, un-permutation and average are linear.
+ * Outputs: loss, dL/dalpha [iters], dL/dLLR [F][n], final y [F][n].
+ * ---------------------------------------------------------------------------- */
+int or_nms_train_grad(const uint8_t *Ho, int M, int n, const float *llr, int ld, int F, int P,
+                      const uint16_t *autos, int iters, const double *alpha, const uint8_t *cw,
+                      double *loss_out, double *dalpha, double *dllr, double *y_out) {
+  double *ys = (double *)malloc(sizeof(double) * (size_t)(iters + 1) * n);
+  if (!ys) return OR_ENOMEM;
+  int vars[128];
+  double rowbuf[128];
+  double loss = 0.0;
+  for (int t = 0; t < iters; t++) dalpha[t] = 0.0;
+  double inv_cnt = 1.0 / ((double)F * (double)n);
+  for (int f = 0; f < F; f++) {
+    const float *L = llr + (size_t)f * ld;
+    const uint16_t *aut = autos + (size_t)f * P;
+    for (int i = 0; i < n; i++) ys[i] = (double)L[i];
+    for (int t = 1; t <= iters; t++)
+      enhanced_iteration(Ho, M, n, P, aut, alpha[t - 1], ys + (size_t)(t - 1) * n,
+                         ys + (size_t)t * n, NULL);
+    const double *yf = ys + (size_t)iters * n;
+    double g[128], gprev[128];
+    for (int i = 0; i < n; i++) {
+      double sgn = 1.0 - 2.0 * (double)cw[(size_t)f * n + i];
+      double x = -sgn * yf[i];
+      double sp = (x > 0.0 ? x : 0.0) + log1p(exp(-fabs(x)));
+      loss += sp;
+      double sig = 1.0 / (1.0 + exp(-x));
+      g[i] = inv_cnt * sig * (-sgn);
+      if (y_out) y_out[(size_t)f * n + i] = yf[i];
+    }
+    for (int t = iters; t >= 1; t--) {
+      const double *yp = ys + (size_t)(t - 1) * n;
+      double at = alpha[t - 1];
+      for (int i = 0; i < n; i++) gprev[i] = g[i];
+      for (int p = 0; p < P; p++) {
+        int pi[128], inv[128];
+        double z[128], gz[128], dz[128];
+        for (int i = 0; i < n; i++) {
+          pi[i] = auto_apply(aut[p], n, i);
+          inv[pi[i]] = i;
+          z[pi[i]] = yp[i];
+        }
+        for (int u = 0; u < n; u++) {
+          gz[u] = g[inv[u]] / (double)P;
+          dz[u] = 0.0;
+        }
+        for (int j = 0; j < M; j++) {
+          int w = row_vars(Ho, n, j, vars);
+          for (int e = 0; e < w; e++) rowbuf[e] = z[vars[e]];
+          for (int e = 0; e < w; e++) {
+            double sg = 1.0, mn = INFINITY;
+            int am = -1;
+            for (int e2 = 0; e2 < w; e2++) {
+              if (e2 == e) continue;
+              if (rowbuf[e2] < 0.0) sg = -sg;
+              if (fabs(rowbuf[e2]) < mn) { mn = fabs(rowbuf[e2]); am = e2; }
+            }
+            double gu = gz[vars[e]];
+            dalpha[t - 1] += gu * sg * mn;
+            double sa = rowbuf[am] < 0.0 ? -1.0 : 1.0;
+            dz[vars[am]] += gu * at * sg * sa;
+          }
+        }
+        for (int i = 0; i < n; i++) gprev[i] += dz[pi[i]];
+      }
+      for (int i = 0; i < n; i++) g[i] = gprev[i];
+    }
+    for (int i = 0; i < n; i++) dllr[(size_t)f * n + i] = g[i];
+  }
+  *loss_out = loss * inv_cnt;
+  free(ys);
+  return OR_OK;
+}

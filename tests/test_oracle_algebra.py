@@ -1,0 +1,234 @@
+"""Pins for the oracle's code algebra: generator / check polynomials, the standard
+parity-check matrix, systematic encoding, and the optimized matrix H_o.
+
+Every expectation here comes from outside the oracle: Table I of arXiv 2412.20828,
+textbook facts about BCH codes (roots of g, deg g = n - k, the BCH(15,7) weight
+enumerator) or brute-force enumeration written independently in numpy.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2412_20828_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+PRIM = {15: (4, 0b10011), 63: (6, 0b1000011), 127: (7, 0b10001001)}
+T_OF = {(15, 7): 2, (63, 36): 5, (63, 45): 3, (127, 64): 10, (127, 78): 7, (127, 99): 4}
+
+
+def _gf_mul(a, b, m, prim):
+    # carry-less multiply then reduce: a route independent of the oracle's log tables
+    r = 0
+    while b:
+        if b & 1:
+            r ^= a
+        b >>= 1
+        a <<= 1
+        if a >> m:
+            a ^= prim
+    return r
+
+
+def _gf_pow(x, e, m, prim):
+    r = 1
+    for _ in range(e):
+        r = _gf_mul(r, x, m, prim)
+    return r
+
+
+def _poly_eval(coeffs, x, m, prim):
+    acc = 0
+    for c in reversed(list(coeffs)):
+        acc = _gf_mul(acc, x, m, prim) ^ int(c)
+    return acc
+
+
+def _read(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _c4(H):
+    ov = H.astype(np.int64) @ H.T.astype(np.int64)
+    iu = np.triu_indices(H.shape[0], 1)
+    o = ov[iu]
+    return int((o * (o - 1) // 2).sum())
+
+
+@pytest.mark.parametrize("row", _read("table1_standard_h.txt"), ids=lambda r: f"{r[0]}_{r[1]}")
+def test_standard_h_matches_table1(row):
+    n, k, rows, rw, cmin, cmax = map(int, row[:6])
+    cmean, cstd, c4 = float(row[6]), float(row[7]), int(row[8])
+    H = O.std_h(n, k)
+    assert H.shape == (rows, n)
+    assert set(H.sum(1)) == {rw}
+    cw = H.sum(0)
+    assert (cw.min(), cw.max()) == (cmin, cmax)
+    assert round(float(cw.mean()), 1) == pytest.approx(cmean)
+    assert round(float(cw.std()), 1) == pytest.approx(cstd)
+    assert _c4(H) == c4
+
+
+@pytest.mark.parametrize("nk", list(T_OF))
+def test_generator_degree_and_roots(nk):
+    n, k = nk
+    t = T_OF[nk]
+    m, prim = PRIM[n]
+    g = O.gen_poly(n, k)
+    assert len(g) - 1 == n - k and g[0] == 1 and g[-1] == 1
+    alpha = 2
+    for e in range(1, 2 * t + 1):
+        assert _poly_eval(g, _gf_pow(alpha, e, m, prim), m, prim) == 0, e
+    # g divides x^n + 1 (Python big-int polynomial division over GF(2))
+    gi = int("".join(str(int(b)) for b in g[::-1]), 2)
+    r = (1 << n) | 1
+    dg = n - k
+    for sh in range(n - dg, -1, -1):
+        if r >> (sh + dg) & 1:
+            r ^= gi << sh
+    assert r == 0
+
+
+@pytest.mark.parametrize("nk", list(T_OF))
+def test_encoder_codewords(nk):
+    n, k = nk
+    t = T_OF[nk]
+    m, prim = PRIM[n]
+    msg = synth.messages(40, k, seed=11)
+    cw = O.encode(n, k, msg)
+    H = O.std_h(n, k)
+    assert np.all((cw.astype(np.int64) @ H.T.astype(np.int64)) % 2 == 0)
+    assert np.array_equal(cw[:, n - k:], msg)  # systematic placement
+    for c in cw[:5]:
+        for e in range(1, 2 * t + 1):
+            assert _poly_eval(c, _gf_pow(2, e, m, prim), m, prim) == 0
+
+
+def test_bch15_7_weight_enumerator():
+    # BCH(15,7), d = 5: A_0..A_15 = 1,0,0,0,0,18,30,15,15,30,18,0,0,0,0,1 (textbook)
+    msg = ((np.arange(128)[:, None] >> np.arange(7)[None, :]) & 1).astype(np.uint8)
+    cw = O.encode(15, 7, msg)
+    hist = np.bincount(cw.sum(1), minlength=16)
+    assert hist.tolist() == [1, 0, 0, 0, 0, 18, 30, 15, 15, 30, 18, 0, 0, 0, 0, 1]
+
+
+def _dual_words_u64(H):
+    """All 2^M dual codewords of a code with n <= 64, bit-packed, by meet in the middle."""
+    M, n = H.shape
+    assert n <= 64
+    rows = np.array([int("".join(str(int(b)) for b in r[::-1]), 2) for r in H], dtype=np.uint64)
+    h1 = M // 2
+    A = np.zeros(1 << h1, np.uint64)
+    for i in range(h1):
+        A[1 << i: 1 << (i + 1)] = A[: 1 << i] ^ rows[i]
+    B = np.zeros(1 << (M - h1), np.uint64)
+    for i in range(M - h1):
+        B[1 << i: 1 << (i + 1)] = B[: 1 << i] ^ rows[h1 + i]
+    return A, B
+
+
+def _unpack(v, n):
+    return np.array([(int(v) >> i) & 1 for i in range(n)], np.uint8)
+
+
+def test_dual_63_45_minimum_weight_and_rank():
+    H = O.std_h(63, 45)
+    A, B = _dual_words_u64(H)
+    allw = (A[:, None] ^ B[None, :]).ravel()
+    w = np.bitwise_count(allw)
+    w[0] = 99
+    assert w.min() == 16 and int((w == 16).sum()) == 189  # 3 cyclic classes of 63
+    mins = np.stack([_unpack(v, 63) for v in allw[w == 16]])
+    assert O.rank(mins) == 18  # uniform minimum-weight rows reach full rank (Sec. III-A)
+
+
+@pytest.mark.slow
+def test_dual_63_36_rank_deficiency():
+    # Sec. III-A: the minimum-weight dual codewords of (63,36) cannot form a full-rank H_o
+    H = O.std_h(63, 36)
+    A, B = _dual_words_u64(H)
+    found = []
+    for b in B:
+        x = A ^ b
+        w = np.bitwise_count(x)
+        if b == 0:
+            w[0] = 99
+        assert w.min() >= 14
+        found.extend(x[w == 14].tolist())
+    assert len(found) == 450
+    mins = np.stack([_unpack(v, 63) for v in found])
+    assert O.rank(mins) == 24 < 27
+
+
+def _generator_rows(n, k):
+    eye = np.eye(k, dtype=np.uint8)
+    return O.encode(n, k, eye)
+
+
+@pytest.fixture(scope="module")
+def ho_cache():
+    return {}
+
+
+def _ho(cache, n, k):
+    if (n, k) not in cache:
+        cache[(n, k)] = O.build_ho(n, k, return_r1=True)
+    return cache[(n, k)]
+
+
+@pytest.mark.parametrize("row", _read("table1_ho_row_weights.txt"), ids=lambda r: f"{r[0]}_{r[1]}")
+def test_ho_invariants_and_table1_row_weights(row, ho_cache):
+    n, k, wmin, wmax = map(int, row)
+    Ho, r1 = _ho(ho_cache, n, k)
+    assert Ho.shape == (2 * (n - k), n)
+    G = _generator_rows(n, k)
+    # every row of H_o is a dual codeword
+    assert np.all((G.astype(np.int64) @ Ho.T.astype(np.int64)) % 2 == 0)
+    assert O.rank(Ho) == n - k
+    rw = Ho.sum(1)
+    assert (rw.min(), rw.max()) == (wmin, wmax)
+    # rows are distinct
+    assert len({r.tobytes() for r in Ho}) == Ho.shape[0]
+
+
+def test_ho_63_45_three_classes(ho_cache):
+    # Sec. III-A / Table I: H_o of (63,45) holds uniform weight-16 rows; with
+    # M_o = M_r1 + beta (M - M_r1) = 33 at beta = 2, M_r1 = 3.
+    Ho, r1 = _ho(ho_cache, 63, 45)
+    assert r1 == 3
+    assert r1 + 2 * (18 - r1) == 33
+    classes = set()
+    for r in Ho:
+        rots = [np.roll(r, q).tobytes() for q in range(63)]
+        classes.add(min(rots))
+    assert len(classes) == 3
+
+
+def test_ho_bch15_7_single_class():
+    # the (15,8) dual code has one weight-4 cyclic class of 15 words; the default row
+    # count 2(n-k) = 16 is clamped to the 15 distinct rows available
+    Ho = O.build_ho(15, 7)
+    assert Ho.shape == (15, 15) and set(Ho.sum(1)) == {4}
+    assert O.rank(Ho) == 8
+
+
+def test_ho_deterministic_and_seeded():
+    a = O.build_ho(63, 36, seed=5)
+    b = O.build_ho(63, 36, seed=5)
+    c = O.build_ho(63, 36, seed=6)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c)
+
+
+def test_ho_explicit_row_count():
+    Ho = O.build_ho(63, 45, m_rows=33)
+    assert Ho.shape == (33, 63) and O.rank(Ho) == 18
+    with pytest.raises(RuntimeError):
+        O.build_ho(63, 45, m_rows=17)  # fewer rows than n - k
