@@ -1,0 +1,277 @@
+/*
+ * bchdec.h -- C ABI of the GB300 (sm_103a) enhanced normalized min-sum decoder for
+ * short BCH codes, after arXiv 2412.20828 (Li & Yu, "Effective Application of
+ * Normalized Min-Sum Decoding for Short BCH Codes").
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns bch_status (BCH_OK = 0); no C++ exception crosses the ABI.
+ *    bch_status_str() names a status; bch_last_error() returns the text of the most
+ *    recent failure on the calling thread.
+ *  - Codes: narrow-sense primitive BCH(n,k), n in {15, 63, 127}, GF(2^m) primitive
+ *    polynomials x^4+x+1, x^6+x+1, x^7+x^3+1.
+ *  - Bit order: bit i of a word is the coefficient of x^i; packed words hold bit i in
+ *    64-bit word i/64, bit i%64.  Codeword layout is systematic: parity in positions
+ *    0..n-k-1, message bit i at position n-k+i.
+ *  - LLR sign (Eq. 1 of the paper): positive means bit 0; L = 2y/sigma^2.
+ *  - Frame arrays are row-major [n_frames][ld] with ld >= n floats; ld a multiple of
+ *    4 and 16-byte-aligned rows give 128-bit loads (ld = 64 for n = 63, 128 for 127).
+ *  - Device-side calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  Pointers documented "device" must be device-accessible memory
+ *    owned by the caller; the library owns only bch_code, bch_decoder and bch_server
+ *    objects and what they allocate.  Decode calls allocate nothing: scratch comes
+ *    from a caller-provided workspace sized by bch_workspace_size().
+ *  - A CUDA error met during an asynchronous call surfaces as BCH_ECUDA from that
+ *    call or a later one (errors are sticky, as in CUDA).
+ */
+#ifndef BCHDEC_H_
+#define BCHDEC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BCH_OK = 0,
+  BCH_EINVAL = 1,   /* bad argument (size, pointer, alignment, unsupported code)  */
+  BCH_ENOMEM = 2,   /* host or device allocation failed (library-owned objects)   */
+  BCH_ECUDA = 3,    /* a CUDA runtime call or kernel failed                        */
+  BCH_ERANK = 4,    /* H_o could not reach rank n-k                                */
+  BCH_ETIMEOUT = 5, /* a bounded device wait or host poll ran out                  */
+  BCH_EBUDGET = 6,  /* request larger than the server's HBM budget                 */
+  BCH_EBUSY = 7     /* server queue full / object in use                           */
+} bch_status;
+
+typedef enum { BCH_PCM_STANDARD = 0, BCH_PCM_OPTIMIZED = 1 } bch_pcm_kind;
+
+/* Storage format of the per-frame LLR state y and of the row minima.
+ *  FP32  float storage.
+ *  FP16  binary16 storage, round-to-nearest-even, saturating at +-65504; the
+ *        check-to-variable sums and the merge of Algorithm 1 stay FP32.
+ *  INT8  8-bit saturating fixed point, LSB = 1/4 (q = clamp(rne(4x), -31, 31));
+ *        minima, signs and check-to-variable values (rne(alpha q)) are integers,
+ *        summed exactly in 16 bits, merged in FP32, re-quantised with saturation. */
+typedef enum { BCH_MSG_FP32 = 0, BCH_MSG_FP16 = 1, BCH_MSG_INT8 = 2 } bch_msg_type;
+
+/* Opaque code object: host and device copies of the standard H or H_o. */
+typedef struct bch_code bch_code;
+
+/* Options of the H_o construction (Sec. III-A, steps 3-6).  NULL = defaults. */
+typedef struct {
+  int q_rounds;      /* rounds of the shifted row-summation search (step 4); default 4   */
+  int sa_steps;      /* simulated-annealing proposals (step 6); default 20000            */
+  double sa_lambda;  /* weight of the column-weight variance in the loss; <= 0 means n  */
+  double sa_t0_frac; /* initial temperature as a fraction of the initial loss; 0.05     */
+  double sa_cool;    /* geometric cooling factor per proposal; default 0.9995           */
+} bch_pcm_opts;
+
+/* Decoder parameters. */
+typedef struct {
+  int iters;           /* maximum iterations I_m, 1..32                                 */
+  const float *alpha;  /* host array of `iters` normalization factors alpha_1..alpha_t   */
+  int n_autos;         /* P = automorphisms per frame, 1..9 (Algorithm 1); 0 selects the
+                          plain flooding decoder of Eqs. (2)-(5) with per-edge messages */
+  int early_stop;      /* 1: stop a frame at the first zero syndrome (Eq. 5)            */
+  bch_msg_type msg;    /* storage format                                                 */
+  int rescale;         /* 1 (FP16/INT8 only): renormalise each frame's y by a power of
+                          two after every merge; min-sum is scale invariant, so only
+                          quantisation changes.  0: plain saturation                     */
+  int osd_order;       /* hybrid decoding only: OSD order 0..2                            */
+} bch_nms_params;
+
+/* Per-frame flag bits written by the decoders. */
+#define BCH_FLAG_CONVERGED 1u /* the NMS hard decision has zero syndrome               */
+#define BCH_FLAG_OSD 2u       /* the final word came from the OSD fallback             */
+
+/* ---------------------------------------------------------------- codes (host) */
+
+/* Build the parity-check matrix of BCH(n,k) on the host and upload it (Sec. III-A).
+ * kind = STANDARD: the (n-k) x n cyclic matrix whose row r holds the reversed check
+ *   polynomial from column r (attributes of Table I, "H" rows).
+ * kind = OPTIMIZED: H_o by steps 1-6 of Sec. III-A: reduced row echelon form;
+ *   heuristic binary row summation; q_rounds rounds with all cyclic shifts; selection
+ *   of the m_rows lightest rows (or padding with randomly shifted copies); simulated
+ *   annealing of cyclic row shifts against (#4-cycles + lambda var(column weights));
+ *   rank repair.  m_rows = 0 selects 2(n-k), clamped to the number of distinct rows
+ *   the search reached.  Deterministic in `seed` (SplitMix64).
+ * Returns BCH_EINVAL for an unsupported (n,k), BCH_ERANK if rank n-k is unreachable.
+ * *out is owned by the caller and released with bch_code_free(). */
+bch_status bch_build_pcm(int n, int k, bch_pcm_kind kind, int m_rows, uint64_t seed,
+                         const bch_pcm_opts *opts, bch_code **out);
+
+/* Host-only variant of bch_build_pcm: runs the same construction and writes the matrix
+ * as bytes (rows x n, row-major) into caller-owned host memory `dense` of `capacity`
+ * bytes; *rows receives the row count.  Touches no GPU. */
+bch_status bch_build_pcm_host(int n, int k, bch_pcm_kind kind, int m_rows, uint64_t seed,
+                              const bch_pcm_opts *opts, uint8_t *dense, size_t capacity,
+                              int *rows);
+
+/* Dimensions of a code object: n, k, rows, edges (ones in the matrix), max row weight. */
+bch_status bch_code_info(const bch_code *code, int *n, int *k, int *rows, int *edges,
+                         int *max_row_weight);
+
+/* Copy the matrix out as bytes (rows x n, caller-owned host memory). */
+bch_status bch_pcm_export(const bch_code *code, uint8_t *dense, size_t capacity);
+
+void bch_code_free(bch_code *code);
+
+/* ---------------------------------------------------------------- automorphisms */
+
+/* Draw P automorphisms per frame (Sec. III-B): pairs (s, j) acting as
+ * pi(i) = (2^j i + s) mod n, j a Frobenius power in [0, ord_n(2)), s a cyclic shift in
+ * [0, n).  Stateless in (seed, frame index, slot): x = SplitMix64 output number
+ * 1 + (f P + p) 16 + a from state `seed`; s = floor(lo32(x) n / 2^32),
+ * j = floor(hi32(x) ord / 2^32); retried (a = 1..15) while the pair repeats an earlier
+ * slot of the frame.  Output packed s | j << 8, layout [n_frames][n_autos].
+ * bch_draw_automorphisms writes device memory on `stream`; the _host variant writes
+ * host memory synchronously.  Both produce identical values. */
+bch_status bch_draw_automorphisms(int n, int n_autos, uint64_t seed, uint64_t frame0,
+                                  int n_frames, uint16_t *out, void *stream);
+bch_status bch_draw_automorphisms_host(int n, int n_autos, uint64_t seed, uint64_t frame0,
+                                       int n_frames, uint16_t *out);
+
+/* ---------------------------------------------------------------- frames */
+
+/* Synthetic BPSK/AWGN frames (Sec. II, Eq. 1) on the device, counter-based:
+ * Philox4x32-10 keyed by seed, counter (frame, block, tag): tag 0 message bits,
+ * tag 1 Box-Muller noise for positions 4b..4b+3, tag 2 a per-frame Eb/N0 uniform in
+ * [ebn0_lo, ebn0_hi) when ebn0_hi > ebn0_lo.  Systematic encoding, s = 1 - 2c,
+ * y = s + sigma n, L = 2y/sigma^2 with sigma^2 = 1/(2 (k/n) 10^(Eb/N0/10)).
+ * llr: device [n_frames][ld] (padding columns written 0); codeword: device
+ * [n_frames][ceil(n/64)] u64 or NULL. */
+bch_status bch_gen_frames(const bch_code *code, float ebn0_lo, float ebn0_hi, uint64_t seed,
+                          uint64_t frame0, int n_frames, float *llr, int ld, uint64_t *codeword,
+                          void *stream);
+
+/* ---------------------------------------------------------------- decoding */
+
+/* Bytes of device scratch a decode call needs (frame queue counters, failed-frame
+ * list of the hybrid decoder, training reductions).  Valid for any call with at most
+ * n_frames frames and the same parameters. */
+bch_status bch_workspace_size(const bch_code *code, const bch_nms_params *params, int n_frames,
+                              size_t *bytes);
+
+/* Enhanced NMS (Algorithm 1), or plain NMS (Eqs. 2-5) when params->n_autos == 0.
+ * Algorithm 1 as implemented (reading A: the only state kept between iterations is y):
+ *   for t = 1..I_m: for each automorphism p, z_p[pi_p(i)] = y[i]; on every edge (j,u)
+ *   of H_o, c2v_p(j,u) = alpha_t prod_{u'!=u} sgn z_p[u'] min_{u'!=u} |z_p[u']|;
+ *   y_t[i] = y[i] + (1/P) sum_p sum_{j: (j,pi_p(i)) edge} c2v_p(j, pi_p(i));
+ *   c = [y_t < 0]; stop if H_o c^T = 0 (and early_stop), else y <- y_t.
+ * llr: device [n_frames][ld] FP32 channel LLRs (read only).
+ * autos: device [n_frames][n_autos] packed pairs (ignored when n_autos == 0).
+ * hard: device [n_frames][ceil(n/64)] u64 final hard decision.
+ * iters: device [n_frames] u8 iterations run.  flags: device [n_frames] u8
+ * (BCH_FLAG_CONVERGED).  llr_out: device [n_frames][ld] final y (FP32) or NULL.
+ * workspace: device, >= bch_workspace_size() bytes, 256-byte aligned.
+ * n_frames = 0 is a no-op.  Frames are independent: the result of a frame does not
+ * depend on the batch it is decoded in. */
+bch_status bch_nms_decode(const bch_code *code, const bch_nms_params *params, const float *llr,
+                          int ld, int n_frames, const uint16_t *autos, uint64_t *hard,
+                          uint8_t *iters, uint8_t *flags, float *llr_out, void *workspace,
+                          void *stream);
+
+/* Hybrid decoder (Sec. IV, complexity discussion): enhanced NMS on `code`; frames
+ * whose NMS hard decision has nonzero syndrome go to order-p OSD (Sec. II-B) on the
+ * standard matrix `std_code`: positions sorted by FP32 |L| ascending (stable);
+ * Gaussian elimination over GF(2) pivots on the least reliable independent columns;
+ * the other k positions form the most reliable basis; every test pattern of weight
+ * <= p on it is re-encoded and scored by sum over disagreeing positions of
+ * floor(|L_i| 2^24) (exact integers); the first minimum wins.  OSD frames get
+ * BCH_FLAG_OSD and their hard decision replaced.  failed_list (optional, device
+ * [n_frames] u32) and failed_count (optional, device u32) receive the OSD frame
+ * indices in ascending order and their count.  No host synchronisation. */
+bch_status bch_hybrid_decode(const bch_code *code, const bch_code *std_code,
+                             const bch_nms_params *params, const float *llr, int ld, int n_frames,
+                             const uint16_t *autos, uint64_t *hard, uint8_t *iters, uint8_t *flags,
+                             float *llr_out, uint32_t *failed_list, uint32_t *failed_count,
+                             void *workspace, void *stream);
+
+/* Failed-frame compaction (the hybrid decoder's hand-off to OSD): writes to list
+ * (device [n_frames] u32) the indices of the frames whose flags lack
+ * BCH_FLAG_CONVERGED, in ascending order, and their number to *count (device u32).
+ * Deterministic two-pass block scan; no host synchronisation. */
+bch_status bch_compact_failed(const uint8_t *flags, int n_frames, uint32_t *list, uint32_t *count,
+                              void *workspace, void *stream);
+
+/* Order-p OSD alone on the listed frames (indices into llr), overwriting their hard
+ * decision; used by the hybrid decoder and exposed for testing. */
+bch_status bch_osd_decode(const bch_code *std_code, int order, const float *llr, int ld,
+                          const uint32_t *frame_list, const uint32_t *count, int max_frames,
+                          uint64_t *hard, uint8_t *flags, void *workspace, void *stream);
+
+/* Per-batch error counters (for FER/BER reporting) accumulated into
+ * counters[8] (device int64): 0 frames, 1 frame errors, 2 bit errors, 3 undetected
+ * errors (converged to a wrong codeword), 4 OSD frames, 5 total iterations,
+ * 6 NMS-converged frames, 7 reserved.  codeword is the transmitted word. */
+bch_status bch_count_errors(int n, const uint64_t *hard, const uint64_t *codeword,
+                            const uint8_t *iters, const uint8_t *flags, int n_frames,
+                            long long *counters, void *stream);
+
+/* ---------------------------------------------------------------- host pipeline */
+
+/* Decoder context for callers whose frames live in host memory.  It owns device
+ * buffers for two chunks of `chunk_frames` frames and two CUDA streams, so the
+ * host-to-device copy of one chunk, the hybrid decode of another and the copy-back
+ * overlap.  params (alpha is copied) and ld are fixed at creation; std_code may be
+ * NULL to run enhanced NMS only (no OSD). */
+typedef struct bch_decoder bch_decoder;
+bch_status bch_decoder_create(const bch_code *code, const bch_code *std_code,
+                              const bch_nms_params *params, int ld, int chunk_frames,
+                              bch_decoder **out);
+/* Decodes n_frames frames from host memory: llr [n_frames][ld] FP32 (page-locked
+ * memory gives full copy bandwidth), automorphisms drawn on the device from
+ * (autos_seed, frame0 + index), results to host arrays hard [n_frames][ceil(n/64)],
+ * iters and flags [n_frames] (iters/flags nullable).  Returns when all results are
+ * in host memory. */
+bch_status bch_decoder_run_host(bch_decoder *dec, const float *llr, int n_frames,
+                                uint64_t autos_seed, uint64_t frame0, uint64_t *hard,
+                                uint8_t *iters, uint8_t *flags);
+void bch_decoder_destroy(bch_decoder *dec);
+
+/* ---------------------------------------------------------------- training */
+
+/* Training forward pass: all `iters` iterations without early stop (FP32 only),
+ * checkpointing y^(0..I_m): ckpt device [iters+1][n_frames][ld] (y^(t) of frame f at
+ * ckpt + (t n_frames + f) ld).  workspace as for bch_nms_decode. */
+bch_status bch_nms_forward_train(const bch_code *code, const bch_nms_params *params,
+                                 const float *llr, int ld, int n_frames, const uint16_t *autos,
+                                 float *ckpt, void *workspace, void *stream);
+
+/* Backward pass through the iterations (subgradient of min-sum): given
+ * grad_out = dLoss/dy^(I_m) [n_frames][ld], writes grad_llr = dLoss/dy^(0)
+ * [n_frames][ld] (nullable) and grad_alpha[iters] (device FP32, overwritten).
+ * d c2v/d alpha_t = c2v/alpha_t; d c2v(j,u)/d z_a = alpha_t prod_{u'!=u} sgn z_u' sgn z_a
+ * at a = argmin over the row without u (lowest column on ties); sign derivatives 0.
+ * Recomputes each iteration from its checkpoint. */
+bch_status bch_nms_backward(const bch_code *code, const bch_nms_params *params,
+                            const uint16_t *autos, const float *ckpt, int ld, int n_frames,
+                            const float *grad_out, float *grad_llr, float *grad_alpha,
+                            void *workspace, void *stream);
+
+/* Binary cross-entropy of the final LLRs against the transmitted word:
+ * loss = mean_i softplus(-(1 - 2c_i) y_i) over frames and bits (device FP32 scalar,
+ * overwritten) and grad = dloss/dy [n_frames][ld]. */
+bch_status bch_bce_loss(int n, const float *y, int ld, const uint64_t *codeword, int n_frames,
+                        float *loss, float *grad, void *workspace, void *stream);
+
+/* Convenience loop: `steps` Adam steps (learning rate lr) on the per-iteration factors
+ * alpha_inout[iters] (host, in/out) using `batch` frames per step generated on the
+ * device at Eb/N0 uniform in [ebn0_lo, ebn0_hi).  loss_hist (host, nullable) gets the
+ * loss of every step.  Allocates its own device buffers. */
+bch_status bch_train_alpha(const bch_code *code, int n_autos, int iters, float *alpha_inout,
+                           int steps, int batch, float ebn0_lo, float ebn0_hi, uint64_t seed,
+                           float lr, float *loss_hist, void *stream);
+
+/* ---------------------------------------------------------------- misc */
+
+const char *bch_status_str(bch_status s);
+const char *bch_last_error(void);
+/* Library version string. */
+const char *bch_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCHDEC_H_ */

@@ -70,7 +70,7 @@ def _load():
             "or_nms_enhanced": (i, [P, i, i, P, i, i, i, P, i, P, i, P, P, P, P, P, P, P]),
             "or_osd": (i, [P, i, i, P, i, i, i, P, P, P]),
             "or_ml": (i, [i, i, P, i, i, P]),
-            "or_nms_train_grad": (i, [P, i, i, P, i, i, i, P, i, P, P, P, P, P, P]),
+            "or_nms_train_grad": (i, [P, i, i, P, i, i, i, P, i, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -305,7 +305,7 @@ def hybrid(Ho, Hstd, llr, autos, iters, alpha, order=2, threads=1):
     return r
 
 
-def train_grad(Ho, llr, autos, iters, alpha, cw):
+def train_grad(Ho, llr, autos, iters, alpha, cw, return_margin=False):
     Ho = np.ascontiguousarray(Ho, np.uint8)
     M, n = Ho.shape
     llr = np.ascontiguousarray(llr, np.float32)
@@ -318,6 +318,9 @@ def train_grad(Ho, llr, autos, iters, alpha, cw):
     da = np.zeros(iters, np.float64)
     dl = np.zeros((F, n), np.float64)
     y = np.zeros((F, n), np.float64)
+    tm = np.zeros(F, np.float64)
     _check(_load().or_nms_train_grad(_p(Ho), M, n, _p(llr), ld, F, P, _p(autos), iters, _p(al),
-                                     _p(cw), _p(loss), _p(da), _p(dl), _p(y)), "train_grad")
+                                     _p(cw), _p(loss), _p(da), _p(dl), _p(y), _p(tm)), "train_grad")
+    if return_margin:
+        return float(loss[0]), da, dl, y, tm
     return float(loss[0]), da, dl, y

@@ -1116,11 +1116,14 @@ int or_ml(int n, int k, const float *llr, int ld, int F, uint8_t *cw_out) {
  *                            the position of the minimum over the row without u
  *                            (lowest column on ties); sign derivatives are zero;
  *   the dilation, un-permutation and average are linear.
- * Outputs: loss, dL/dalpha [iters], dL/dLLR [F][n], final y [F][n].
+ * Outputs: loss, dL/dalpha [iters], dL/dLLR [F][n], final y [F][n], and per frame the
+ * smallest gap, relative to the row's largest |z|, between a row's two smallest |z|
+ * or between the smallest |z| and zero (where the subgradient is not unique).
  * ---------------------------------------------------------------------------- */
 int or_nms_train_grad(const uint8_t *Ho, int M, int n, const float *llr, int ld, int F, int P,
                       const uint16_t *autos, int iters, const double *alpha, const uint8_t *cw,
-                      double *loss_out, double *dalpha, double *dllr, double *y_out) {
+                      double *loss_out, double *dalpha, double *dllr, double *y_out,
+                      double *tie_margin) {
   double *ys = (double *)malloc(sizeof(double) * (size_t)(iters + 1) * n);
   if (!ys) return OR_ENOMEM;
   int vars[128];
@@ -1146,6 +1149,7 @@ int or_nms_train_grad(const uint8_t *Ho, int M, int n, const float *llr, int ld,
       g[i] = inv_cnt * sig * (-sgn);
       if (y_out) y_out[(size_t)f * n + i] = yf[i];
     }
+    double tm = INFINITY; /* smallest relative gap between a row's two smallest |z| */
     for (int t = iters; t >= 1; t--) {
       const double *yp = ys + (size_t)(t - 1) * n;
       double at = alpha[t - 1];
@@ -1164,7 +1168,19 @@ int or_nms_train_grad(const uint8_t *Ho, int M, int n, const float *llr, int ld,
         }
         for (int j = 0; j < M; j++) {
           int w = row_vars(Ho, n, j, vars);
-          for (int e = 0; e < w; e++) rowbuf[e] = z[vars[e]];
+          double s1 = INFINITY, s2 = INFINITY, sc = 0.0;
+          for (int e = 0; e < w; e++) {
+            rowbuf[e] = z[vars[e]];
+            double a = fabs(rowbuf[e]);
+            if (a > sc) sc = a;
+            if (a < s1) { s2 = s1; s1 = a; } else if (a < s2) s2 = a;
+          }
+          {
+            double g1 = (s2 - s1) / (sc > 1.0 ? sc : 1.0);
+            double g0 = s1 / (sc > 1.0 ? sc : 1.0);
+            if (g1 < tm) tm = g1;
+            if (g0 < tm) tm = g0;
+          }
           for (int e = 0; e < w; e++) {
             double sg = 1.0, mn = INFINITY;
             int am = -1;
@@ -1184,6 +1200,7 @@ int or_nms_train_grad(const uint8_t *Ho, int M, int n, const float *llr, int ld,
       for (int i = 0; i < n; i++) g[i] = gprev[i];
     }
     for (int i = 0; i < n; i++) dllr[(size_t)f * n + i] = g[i];
+    if (tie_margin) tie_margin[f] = tm;
   }
   *loss_out = loss * inv_cnt;
   free(ys);

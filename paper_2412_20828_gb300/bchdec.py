@@ -1,0 +1,364 @@
+"""Thin Python binding of the C ABI in ``include/bchdec.h`` (ctypes).
+
+Argument marshalling only: every step of decoding runs in the CUDA library.  Device
+buffers are torch CUDA tensors (torch is used for memory and streams); the calls are
+asynchronous on the current torch stream unless ``stream`` is given.  Loading fails
+loudly when ``libbchdec.so`` has not been built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbchdec.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ERANK, ETIMEOUT, EBUDGET, EBUSY = range(8)
+PCM_STANDARD, PCM_OPTIMIZED = 0, 1
+MSG_FP32, MSG_FP16, MSG_INT8 = 0, 1, 2
+FLAG_CONVERGED, FLAG_OSD = 1, 2
+
+# Every symbol the header declares (checked by the tests without a GPU).
+EXPORTS = (
+    "bch_build_pcm", "bch_build_pcm_host", "bch_code_info", "bch_pcm_export", "bch_code_free",
+    "bch_draw_automorphisms", "bch_draw_automorphisms_host", "bch_gen_frames",
+    "bch_workspace_size", "bch_nms_decode", "bch_hybrid_decode", "bch_osd_decode",
+    "bch_compact_failed", "bch_count_errors", "bch_nms_forward_train", "bch_nms_backward", "bch_bce_loss",
+    "bch_train_alpha", "bch_decoder_create", "bch_decoder_run_host", "bch_decoder_destroy",
+    "bch_status_str", "bch_last_error", "bch_version",
+)
+
+
+class BchError(RuntimeError):
+    def __init__(self, status, where, detail):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class PcmOpts(C.Structure):
+    _fields_ = [("q_rounds", C.c_int), ("sa_steps", C.c_int), ("sa_lambda", C.c_double),
+                ("sa_t0_frac", C.c_double), ("sa_cool", C.c_double)]
+
+
+class NmsParams(C.Structure):
+    _fields_ = [("iters", C.c_int), ("alpha", C.POINTER(C.c_float)), ("n_autos", C.c_int),
+                ("early_stop", C.c_int), ("msg", C.c_int), ("rescale", C.c_int),
+                ("osd_order", C.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Loads libbchdec.so (built by ``paper_2412_20828_gb300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+        lib = C.CDLL(LIB_PATH)
+        P, i, u64, f, sz = C.c_void_p, C.c_int, C.c_uint64, C.c_float, C.c_size_t
+        st = C.c_int
+        sig = {
+            "bch_build_pcm": (st, [i, i, i, i, u64, C.POINTER(PcmOpts), C.POINTER(P)]),
+            "bch_build_pcm_host": (st, [i, i, i, i, u64, C.POINTER(PcmOpts), P, sz, C.POINTER(i)]),
+            "bch_code_info": (st, [P, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i),
+                                   C.POINTER(i)]),
+            "bch_pcm_export": (st, [P, P, sz]),
+            "bch_code_free": (None, [P]),
+            "bch_draw_automorphisms": (st, [i, i, u64, u64, i, P, P]),
+            "bch_draw_automorphisms_host": (st, [i, i, u64, u64, i, P]),
+            "bch_gen_frames": (st, [P, f, f, u64, u64, i, P, i, P, P]),
+            "bch_workspace_size": (st, [P, C.POINTER(NmsParams), i, C.POINTER(sz)]),
+            "bch_nms_decode": (st, [P, C.POINTER(NmsParams), P, i, i, P, P, P, P, P, P, P]),
+            "bch_hybrid_decode": (st, [P, P, C.POINTER(NmsParams), P, i, i, P, P, P, P, P, P, P,
+                                       P, P]),
+            "bch_osd_decode": (st, [P, i, P, i, P, P, i, P, P, P, P]),
+            "bch_compact_failed": (st, [P, i, P, P, P, P]),
+            "bch_count_errors": (st, [i, P, P, P, P, i, P, P]),
+            "bch_nms_forward_train": (st, [P, C.POINTER(NmsParams), P, i, i, P, P, P, P]),
+            "bch_nms_backward": (st, [P, C.POINTER(NmsParams), P, P, i, i, P, P, P, P, P]),
+            "bch_bce_loss": (st, [i, P, i, P, i, P, P, P, P]),
+            "bch_train_alpha": (st, [P, i, i, P, i, i, f, f, u64, f, P, P]),
+            "bch_decoder_create": (st, [P, P, C.POINTER(NmsParams), i, i, C.POINTER(P)]),
+            "bch_decoder_run_host": (st, [P, P, i, u64, u64, P, P, P]),
+            "bch_decoder_destroy": (None, [P]),
+            "bch_status_str": (C.c_char_p, [i]),
+            "bch_last_error": (C.c_char_p, []),
+            "bch_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, where):
+    if rc != OK:
+        lib = load()
+        raise BchError(rc, where, lib.bch_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor / numpy array (None stays NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t
+
+
+class Code:
+    """A BCH code object (standard H or optimized H_o) owned by the library."""
+
+    def __init__(self, n, k, kind=PCM_OPTIMIZED, m_rows=0, seed=0x2412_20828, q_rounds=4,
+                 sa_steps=20000, sa_lambda=0.0, sa_t0_frac=0.05, sa_cool=0.9995):
+        lib = load()
+        self._h = C.c_void_p()
+        opts = PcmOpts(q_rounds, sa_steps, sa_lambda, sa_t0_frac, sa_cool)
+        _check(lib.bch_build_pcm(n, k, kind, m_rows, seed, C.byref(opts), C.byref(self._h)),
+               "bch_build_pcm")
+        a = [C.c_int() for _ in range(5)]
+        _check(lib.bch_code_info(self._h, *[C.byref(x) for x in a]), "bch_code_info")
+        self.n, self.k, self.rows, self.edges, self.max_row_weight = (x.value for x in a)
+        self.kind = kind
+
+    @property
+    def handle(self):
+        return self._h
+
+    def dense(self) -> np.ndarray:
+        out = np.zeros((self.rows, self.n), np.uint8)
+        _check(load().bch_pcm_export(self._h, _ptr(out), out.nbytes), "bch_pcm_export")
+        return out
+
+    def close(self):
+        if self._h:
+            load().bch_code_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_pcm(n, k, kind=PCM_OPTIMIZED, m_rows=0, seed=0x2412_20828, **opts) -> Code:
+    return Code(n, k, kind, m_rows, seed, **opts)
+
+
+def build_pcm_host(n, k, kind=PCM_OPTIMIZED, m_rows=0, seed=0x2412_20828, q_rounds=4,
+                   sa_steps=20000, sa_lambda=0.0, sa_t0_frac=0.05, sa_cool=0.9995) -> np.ndarray:
+    """The matrix of bch_build_pcm computed on the host only (no GPU), as bytes."""
+    rows_cap = max(m_rows, 2 * (n - k))
+    out = np.zeros((rows_cap, n), np.uint8)
+    rows = C.c_int()
+    opts = PcmOpts(q_rounds, sa_steps, sa_lambda, sa_t0_frac, sa_cool)
+    _check(load().bch_build_pcm_host(n, k, kind, m_rows, seed, C.byref(opts), _ptr(out), out.nbytes,
+                                     C.byref(rows)), "bch_build_pcm_host")
+    return np.ascontiguousarray(out[: rows.value])
+
+
+def params(iters, alpha, n_autos=3, early_stop=True, msg=MSG_FP32, rescale=False, osd_order=2):
+    """Builds a bch_nms_params; ``alpha`` is a scalar or one factor per iteration."""
+    al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float32), (iters,)))
+    p = NmsParams(iters, al.ctypes.data_as(C.POINTER(C.c_float)), n_autos, int(early_stop), msg,
+                  int(rescale), osd_order)
+    p._alpha_keepalive = al  # the C struct points into this array
+    return p
+
+
+def workspace_size(code: Code, p: NmsParams, n_frames: int) -> int:
+    b = C.c_size_t()
+    _check(load().bch_workspace_size(code.handle, C.byref(p), n_frames, C.byref(b)),
+           "bch_workspace_size")
+    return b.value
+
+
+def workspace(code: Code, p: NmsParams, n_frames: int, device="cuda"):
+    import torch
+    nb = workspace_size(code, p, n_frames)
+    return torch.empty(max(nb, 256), dtype=torch.uint8, device=device)
+
+
+def draw_automorphisms(n, n_autos, seed, frame0, out, stream=None):
+    import torch
+    _dev(out, torch.int16, "out")
+    F = out.shape[0]
+    _check(load().bch_draw_automorphisms(n, n_autos, seed, frame0, F, _ptr(out), _stream(stream)),
+           "bch_draw_automorphisms")
+    return out
+
+
+def draw_automorphisms_host(n, n_autos, seed, frame0, n_frames) -> np.ndarray:
+    out = np.zeros((n_frames, n_autos), np.uint16)
+    _check(load().bch_draw_automorphisms_host(n, n_autos, seed, frame0, n_frames, _ptr(out)),
+           "bch_draw_automorphisms_host")
+    return out
+
+
+def gen_frames(code: Code, ebn0_lo, ebn0_hi, seed, frame0, llr, codeword=None, stream=None):
+    import torch
+    _dev(llr, torch.float32, "llr")
+    _dev(codeword, torch.int64, "codeword")
+    F, ld = llr.shape
+    _check(load().bch_gen_frames(code.handle, float(ebn0_lo), float(ebn0_hi), seed, frame0, F,
+                                 _ptr(llr), ld, _ptr(codeword), _stream(stream)), "bch_gen_frames")
+
+
+def nms_decode(code: Code, p: NmsParams, llr, autos, hard, iters=None, flags=None, llr_out=None,
+               ws=None, stream=None):
+    import torch
+    _dev(llr, torch.float32, "llr")
+    _dev(hard, torch.int64, "hard")
+    F, ld = llr.shape
+    ws = ws if ws is not None else workspace(code, p, F)
+    _check(load().bch_nms_decode(code.handle, C.byref(p), _ptr(llr), ld, F, _ptr(autos), _ptr(hard),
+                                 _ptr(iters), _ptr(flags), _ptr(llr_out), _ptr(ws), _stream(stream)),
+           "bch_nms_decode")
+
+
+def hybrid_decode(code: Code, std_code: Code, p: NmsParams, llr, autos, hard, iters, flags,
+                  llr_out=None, failed_list=None, failed_count=None, ws=None, stream=None):
+    import torch
+    _dev(llr, torch.float32, "llr")
+    F, ld = llr.shape
+    ws = ws if ws is not None else workspace(code, p, F)
+    _check(load().bch_hybrid_decode(code.handle, std_code.handle, C.byref(p), _ptr(llr), ld, F,
+                                    _ptr(autos), _ptr(hard), _ptr(iters), _ptr(flags),
+                                    _ptr(llr_out), _ptr(failed_list), _ptr(failed_count), _ptr(ws),
+                                    _stream(stream)), "bch_hybrid_decode")
+
+
+def osd_decode(std_code: Code, order, llr, frame_list, count, hard, flags=None, ws=None,
+               stream=None):
+    import torch
+    F, ld = llr.shape
+    ws = ws if ws is not None else torch.zeros(256, dtype=torch.uint8, device=llr.device)
+    _check(load().bch_osd_decode(std_code.handle, order, _ptr(llr), ld, _ptr(frame_list),
+                                 _ptr(count), frame_list.shape[0], _ptr(hard), _ptr(flags),
+                                 _ptr(ws), _stream(stream)), "bch_osd_decode")
+
+
+def compact_failed(flags, lst, count, ws, n_frames=None, stream=None):
+    F = flags.shape[0] if n_frames is None else n_frames
+    _check(load().bch_compact_failed(_ptr(flags), F, _ptr(lst), _ptr(count), _ptr(ws),
+                                     _stream(stream)), "bch_compact_failed")
+
+
+def count_errors(n, hard, codeword, iters, flags, counters, stream=None):
+    F = hard.shape[0]
+    _check(load().bch_count_errors(n, _ptr(hard), _ptr(codeword), _ptr(iters), _ptr(flags), F,
+                                   _ptr(counters), _stream(stream)), "bch_count_errors")
+
+
+def nms_forward_train(code: Code, p: NmsParams, llr, autos, ckpt, ws=None, stream=None):
+    F, ld = llr.shape
+    ws = ws if ws is not None else workspace(code, p, F)
+    _check(load().bch_nms_forward_train(code.handle, C.byref(p), _ptr(llr), ld, F, _ptr(autos),
+                                        _ptr(ckpt), _ptr(ws), _stream(stream)),
+           "bch_nms_forward_train")
+
+
+def nms_backward(code: Code, p: NmsParams, autos, ckpt, grad_out, grad_llr, grad_alpha, ws=None,
+                 stream=None):
+    F, ld = grad_out.shape
+    ws = ws if ws is not None else workspace(code, p, F)
+    _check(load().bch_nms_backward(code.handle, C.byref(p), _ptr(autos), _ptr(ckpt), ld, F,
+                                   _ptr(grad_out), _ptr(grad_llr), _ptr(grad_alpha), _ptr(ws),
+                                   _stream(stream)), "bch_nms_backward")
+
+
+def bce_loss(n, y, codeword, loss, grad, ws, stream=None):
+    F, ld = y.shape
+    _check(load().bch_bce_loss(n, _ptr(y), ld, _ptr(codeword), F, _ptr(loss), _ptr(grad), _ptr(ws),
+                               _stream(stream)), "bch_bce_loss")
+
+
+def train_alpha(code: Code, n_autos, iters, alpha, steps, batch, ebn0_lo, ebn0_hi, seed, lr,
+                stream=None):
+    al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float32), (iters,))).copy()
+    hist = np.zeros(max(steps, 1), np.float32)
+    _check(load().bch_train_alpha(code.handle, n_autos, iters, _ptr(al), steps, batch,
+                                  float(ebn0_lo), float(ebn0_hi), seed, float(lr), _ptr(hist),
+                                  _stream(stream)), "bch_train_alpha")
+    return al, hist[:steps]
+
+
+class HostDecoder:
+    """bch_decoder: decodes frames held in host memory with overlapped transfers."""
+
+    def __init__(self, code: Code, std_code, p: NmsParams, ld: int, chunk_frames: int = 1 << 20):
+        self._h = C.c_void_p()
+        self._p = p
+        self.code, self.std = code, std_code
+        _check(load().bch_decoder_create(code.handle, std_code.handle if std_code else None,
+                                         C.byref(p), ld, chunk_frames, C.byref(self._h)),
+               "bch_decoder_create")
+        self.ld = ld
+
+    def run(self, llr, autos_seed, frame0, hard, iters=None, flags=None):
+        """llr / hard / iters / flags: host numpy arrays or pinned CPU torch tensors."""
+        F = llr.shape[0]
+        _check(load().bch_decoder_run_host(self._h, _ptr(llr), F, autos_seed, frame0, _ptr(hard),
+                                           _ptr(iters), _ptr(flags)), "bch_decoder_run_host")
+
+    def close(self):
+        if self._h:
+            load().bch_decoder_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unpack_bits(words: np.ndarray, n: int) -> np.ndarray:
+    """[F, ceil(n/64)] packed words (int64/uint64) -> [F, n] uint8 bits."""
+    w = np.ascontiguousarray(words).view(np.uint64).reshape(words.shape[0], -1)
+    bits = np.zeros((w.shape[0], n), np.uint8)
+    for i in range(n):
+        bits[:, i] = (w[:, i >> 6] >> np.uint64(i & 63)) & np.uint64(1)
+    return bits
+
+
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """[F, n] bits -> [F, ceil(n/64)] int64 words (bit i of word i//64)."""
+    F, n = bits.shape
+    W = (n + 63) // 64
+    out = np.zeros((F, W), np.uint64)
+    for i in range(n):
+        out[:, i >> 6] |= bits[:, i].astype(np.uint64) << np.uint64(i & 63)
+    return out.view(np.int64)

@@ -1,0 +1,77 @@
+// Kernel argument blocks and launchers shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bch_internal.h"
+
+namespace bchlib {
+
+struct NmsArgs {
+  DevCode dc;
+  const float *llr;
+  int ld, F;
+  const uint16_t *autos;
+  int P;
+  uint64_t *hard;
+  uint8_t *iters;
+  uint8_t *flags;
+  float *llr_out;
+  float *ckpt;  // training checkpoints [I+1][F][ld] or null
+  unsigned *queue;
+  int I, early_stop, msg, rescale;
+  float alpha[32];
+};
+
+struct OsdArgs {
+  int n, k, M;
+  const uint4 *rows;  // [M] standard H rows, 4 x u32
+  const float *llr;
+  int ld;
+  const uint32_t *list;
+  const uint32_t *count;
+  int max_frames;
+  int order;
+  uint64_t *hard;
+  uint8_t *flags;
+  unsigned *queue;
+};
+
+struct GenArgs {
+  int n, k;
+  const uint64_t *par;  // [k] parity words
+  float ebn0_lo, ebn0_hi;
+  uint64_t seed, frame0;
+  int F, ld;
+  float *llr;
+  uint64_t *codeword;
+};
+
+struct BwdArgs {
+  DevCode dc;
+  const uint16_t *autos;
+  int P;
+  const float *ckpt;
+  int ld, F, I;
+  const float *grad_out;
+  float *grad_llr;
+  float *partial;  // [blocks][I]
+  float alpha[32];
+};
+
+cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st);
+cudaError_t launch_osd(const OsdArgs &a, cudaStream_t st);
+cudaError_t launch_compact(const uint8_t *flags, int F, uint32_t *counts, uint32_t *list,
+                           uint32_t *count, cudaStream_t st);
+cudaError_t launch_draw_autos(int n, int ord, int P, uint64_t seed, uint64_t frame0, int F,
+                              uint16_t *out, cudaStream_t st);
+cudaError_t launch_gen_frames(const GenArgs &a, cudaStream_t st);
+cudaError_t launch_count_errors(int n, const uint64_t *hard, const uint64_t *cw, const uint8_t *iters,
+                                const uint8_t *flags, int F, long long *counters, cudaStream_t st);
+cudaError_t launch_bce(int n, const float *y, int ld, const uint64_t *cw, int F, float *loss,
+                       float *grad, float *partial, cudaStream_t st);
+size_t bce_workspace(int F);
+cudaError_t launch_backward(const BwdArgs &a, float *grad_alpha, cudaStream_t st);
+size_t backward_workspace(int F, int I);
+
+}  // namespace bchlib

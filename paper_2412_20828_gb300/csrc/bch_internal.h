@@ -1,0 +1,104 @@
+// Internal declarations shared by the library's translation units (host algebra,
+// C-ABI layer and CUDA kernels).  Not installed; not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bchdec.h"
+
+namespace bchlib {
+
+// A row of at most 128 bits: bit i = coefficient of x^i.
+struct Row {
+  uint64_t w[2] = {0, 0};
+  bool get(int i) const { return (w[i >> 6] >> (i & 63)) & 1u; }
+  void set(int i) { w[i >> 6] |= uint64_t(1) << (i & 63); }
+  void flip(int i) { w[i >> 6] ^= uint64_t(1) << (i & 63); }
+  int weight() const { return __builtin_popcountll(w[0]) + __builtin_popcountll(w[1]); }
+  bool zero() const { return (w[0] | w[1]) == 0; }
+  Row operator^(const Row &o) const {
+    Row r;
+    r.w[0] = w[0] ^ o.w[0];
+    r.w[1] = w[1] ^ o.w[1];
+    return r;
+  }
+  Row operator&(const Row &o) const {
+    Row r;
+    r.w[0] = w[0] & o.w[0];
+    r.w[1] = w[1] & o.w[1];
+    return r;
+  }
+  bool operator==(const Row &o) const { return w[0] == o.w[0] && w[1] == o.w[1]; }
+  bool operator<(const Row &o) const { return w[1] != o.w[1] ? w[1] < o.w[1] : w[0] < o.w[0]; }
+};
+
+// Cyclic rotation by q (multiplication by x^q modulo x^n - 1).
+Row rotate(const Row &r, int n, int q);
+
+struct CodeAlgebra {
+  int n = 0, k = 0, m = 0, ord = 0;
+  std::vector<uint8_t> g;    // generator polynomial, n-k+1 coefficients
+  std::vector<uint8_t> h;    // check polynomial, k+1 coefficients
+  std::vector<Row> std_h;    // (n-k) standard rows
+  std::vector<uint64_t> par; // parity word contributed by message bit i (n-k <= 64 bits)
+};
+
+// Returns false (with a message) for unsupported (n, k).
+bool make_algebra(int n, int k, CodeAlgebra *out, std::string *err);
+
+struct HoOptions {
+  int q_rounds = 4;
+  int sa_steps = 20000;
+  double sa_lambda = 0.0;  // <= 0 -> n
+  double sa_t0_frac = 0.05;
+  double sa_cool = 0.9995;
+};
+
+// Builds H_o; returns BCH_OK, BCH_EINVAL or BCH_ERANK.
+bch_status build_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoOptions &opt,
+                    std::vector<Row> *rows, int *r1_count, std::string *err);
+
+int gf2_rank(std::vector<Row> rows, int n);
+
+uint64_t splitmix64_next(uint64_t *state);
+uint64_t splitmix64_mix(uint64_t z);
+void draw_autos_host(int n, int P, uint64_t seed, uint64_t frame0, int F, uint16_t *out);
+
+// ----------------------------------------------------------------- device layout
+// Layout of a code object on the device (one allocation, 256-byte aligned pieces).
+// Rows are grouped by weight; each group stores its rows' column codes
+// d(u) = u | u << m (so that the Frobenius power j of u, rotr_m(u, j), is the m-bit
+// field of d(u) starting at bit j) contiguously.
+constexpr int kMaxGroups = 16;
+constexpr int kMaxN = 127;
+
+struct DevCode {
+  int n, k, m, rows, edges, max_w, nwords32;
+  int n_groups;
+  int group_w[kMaxGroups];     // row weight of the group
+  int group_rows[kMaxGroups];  // number of rows
+  int group_off[kMaxGroups + 1];  // offset into codes (in entries); [n_groups] = end
+  const uint16_t *codes;       // [edges] column codes, group order
+  const uint32_t *rowmask;     // [rows][4] bit-packed rows (syndrome test)
+  const uint64_t *par;         // [k] parity words (systematic encoder)
+};
+
+}  // namespace bchlib
+
+struct bch_code {
+  bchlib::CodeAlgebra alg;
+  bch_pcm_kind kind;
+  std::vector<bchlib::Row> rows;  // host copy, final row order
+  int r1_count = 0;
+  void *dev_blob = nullptr;  // device allocation holding the arrays below
+  bchlib::DevCode dc;        // host-side descriptor with device pointers
+  bchlib::DevCode *dev_dc = nullptr;  // descriptor copy in device memory
+};
+
+namespace bchlib {
+void set_error(const std::string &msg);
+bch_status fail(bch_status s, const std::string &msg);
+}  // namespace bchlib

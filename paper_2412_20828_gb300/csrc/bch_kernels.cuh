@@ -1,0 +1,62 @@
+// Device-side helpers shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bch_args.h"
+#include "bch_internal.h"
+
+namespace bchlib {
+
+constexpr uint32_t kSign = 0x80000000u;
+constexpr unsigned kFull = 0xffffffffu;
+
+// m-bit field of x starting at bit `pos` (PTX bfe).
+__device__ __forceinline__ uint32_t bfe32(uint32_t x, uint32_t pos, uint32_t len) {
+  uint32_t r;
+  asm("bfe.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(pos), "r"(len));
+  return r;
+}
+
+// (a + b) mod n for a, b in [0, n): min(a + b, a + b - n) in unsigned arithmetic.
+__device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, uint32_t n) {
+  uint32_t x = a + b;
+  return __viaddmin_u32(x, 0u - n, x);
+}
+
+__device__ __forceinline__ float flip_sign(float mag, uint32_t sign_src) {
+  return __uint_as_float(__float_as_uint(mag) ^ (sign_src & kSign));
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): two 32x32 multiplies per round,
+// key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Open-interval uniform from the top 24 bits: ((w >> 8) + 0.5) 2^-24, exact in FP32.
+__device__ __forceinline__ float u24(uint32_t w) {
+  return (float(w >> 8) + 0.5f) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ uint64_t splitmix64_mix_d(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace bchlib

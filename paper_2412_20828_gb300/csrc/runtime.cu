@@ -1,0 +1,133 @@
+// Host-memory decode pipeline (bch_decoder): chunked copy-in / hybrid decode /
+// copy-out on two CUDA streams so transfers overlap the kernels of the other chunk.
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bch_kernels.cuh"
+
+using namespace bchlib;
+
+struct bch_decoder {
+  const bch_code *code = nullptr;
+  const bch_code *std_code = nullptr;
+  bch_nms_params params{};
+  std::vector<float> alpha;
+  int ld = 0, chunk = 0, W64 = 1;
+  cudaStream_t st[2] = {nullptr, nullptr};
+  struct Slot {
+    float *llr = nullptr;
+    uint16_t *autos = nullptr;
+    uint64_t *hard = nullptr;
+    uint8_t *iters = nullptr;
+    uint8_t *flags = nullptr;
+    void *ws = nullptr;
+  } slot[2];
+};
+
+namespace {
+void free_decoder(bch_decoder *d) {
+  for (int b = 0; b < 2; b++) {
+    cudaFree(d->slot[b].llr);
+    cudaFree(d->slot[b].autos);
+    cudaFree(d->slot[b].hard);
+    cudaFree(d->slot[b].iters);
+    cudaFree(d->slot[b].flags);
+    cudaFree(d->slot[b].ws);
+    if (d->st[b]) cudaStreamDestroy(d->st[b]);
+  }
+  delete d;
+}
+}  // namespace
+
+extern "C" {
+
+bch_status bch_decoder_create(const bch_code *code, const bch_code *std_code,
+                              const bch_nms_params *params, int ld, int chunk_frames,
+                              bch_decoder **out) {
+  if (!out || !code || !params || !params->alpha) return fail(BCH_EINVAL, "null argument");
+  *out = nullptr;
+  if (chunk_frames < 1 || ld < code->alg.n) return fail(BCH_EINVAL, "bad chunk or ld");
+  if (params->iters < 1 || params->iters > 32) return fail(BCH_EINVAL, "iters must be in [1, 32]");
+  bch_decoder *d = new (std::nothrow) bch_decoder();
+  if (!d) return fail(BCH_ENOMEM, "host allocation");
+  d->code = code;
+  d->std_code = std_code;
+  d->params = *params;
+  d->alpha.assign(params->alpha, params->alpha + params->iters);
+  d->params.alpha = d->alpha.data();
+  d->ld = ld;
+  d->chunk = chunk_frames;
+  d->W64 = (code->alg.n + 63) / 64;
+  size_t wsb = 0;
+  bch_status s = bch_workspace_size(code, &d->params, chunk_frames, &wsb);
+  if (s != BCH_OK) {
+    delete d;
+    return s;
+  }
+  const size_t F = size_t(chunk_frames);
+  const int P = params->n_autos > 0 ? params->n_autos : 1;
+  for (int b = 0; b < 2; b++) {
+    auto &S = d->slot[b];
+    bool ok = cudaStreamCreateWithFlags(&d->st[b], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&S.llr, F * ld * 4) == cudaSuccess &&
+              cudaMalloc(&S.autos, F * P * 2) == cudaSuccess &&
+              cudaMalloc(&S.hard, F * d->W64 * 8) == cudaSuccess &&
+              cudaMalloc(&S.iters, F) == cudaSuccess && cudaMalloc(&S.flags, F) == cudaSuccess &&
+              cudaMalloc(&S.ws, wsb) == cudaSuccess;
+    if (!ok) {
+      free_decoder(d);
+      return fail(BCH_ENOMEM, "decoder buffers");
+    }
+  }
+  *out = d;
+  return BCH_OK;
+}
+
+bch_status bch_decoder_run_host(bch_decoder *d, const float *llr, int n_frames, uint64_t autos_seed,
+                                uint64_t frame0, uint64_t *hard, uint8_t *iters, uint8_t *flags) {
+  if (!d) return fail(BCH_EINVAL, "null decoder");
+  if (n_frames < 0 || (n_frames > 0 && (!llr || !hard))) return fail(BCH_EINVAL, "bad arguments");
+  const int n = d->code->alg.n;
+  const int nchunks = (n_frames + d->chunk - 1) / d->chunk;
+  for (int c = 0; c < nchunks; c++) {
+    const int b = c & 1;
+    auto &S = d->slot[b];
+    cudaStream_t st = d->st[b];
+    const int f0 = c * d->chunk;
+    const int F = std::min(d->chunk, n_frames - f0);
+    cudaError_t e = cudaMemcpyAsync(S.llr, llr + size_t(f0) * d->ld, size_t(F) * d->ld * 4,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("copy in: ") + cudaGetErrorString(e));
+    bch_status s = BCH_OK;
+    if (d->params.n_autos > 0)
+      s = bch_draw_automorphisms(n, d->params.n_autos, autos_seed, frame0 + uint64_t(f0), F, S.autos, st);
+    if (s != BCH_OK) return s;
+    if (d->std_code)
+      s = bch_hybrid_decode(d->code, d->std_code, &d->params, S.llr, d->ld, F, S.autos, S.hard, S.iters,
+                            S.flags, nullptr, nullptr, nullptr, S.ws, st);
+    else
+      s = bch_nms_decode(d->code, &d->params, S.llr, d->ld, F, S.autos, S.hard, S.iters, S.flags, nullptr,
+                         S.ws, st);
+    if (s != BCH_OK) return s;
+    e = cudaMemcpyAsync(hard + size_t(f0) * d->W64, S.hard, size_t(F) * d->W64 * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && iters) e = cudaMemcpyAsync(iters + f0, S.iters, F, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags + f0, S.flags, F, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("copy out: ") + cudaGetErrorString(e));
+  }
+  for (int b = 0; b < 2; b++) {
+    cudaError_t e = cudaStreamSynchronize(d->st[b]);
+    if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("decoder: ") + cudaGetErrorString(e));
+  }
+  return BCH_OK;
+}
+
+void bch_decoder_destroy(bch_decoder *d) {
+  if (!d) return;
+  cudaStreamSynchronize(d->st[0]);
+  cudaStreamSynchronize(d->st[1]);
+  free_decoder(d);
+}
+
+}  // extern "C"

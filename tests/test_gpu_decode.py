@@ -1,0 +1,293 @@
+"""GPU parity of the decoding path (called through the C ABI) against the FP64 oracle:
+automorphism draws, frame generation, enhanced NMS (Algorithm 1), plain NMS
+(Eqs. 2-5), OSD and the hybrid decoder, plus edge cases."""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import ambiguous_frames, autos_dev, frames, rel_close, to_dev
+from paper_2412_20828_gb300 import bchdec as B
+
+pytestmark = pytest.mark.gpu
+
+CODES = [(15, 7), (63, 36), (63, 45), (127, 64), (127, 99)]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2412_20828_gb300 import build
+    build.build()
+    B.load()
+    return torch
+
+
+_codes = {}
+
+
+def code(n, k, kind=B.PCM_OPTIMIZED):
+    key = (n, k, kind)
+    if key not in _codes:
+        _codes[key] = B.Code(n, k, kind=kind)
+    return _codes[key]
+
+
+def W64(n):
+    return (n + 63) // 64
+
+
+def run_nms(torch, c, llr, autos, iters, alpha, early_stop=True, msg=B.MSG_FP32, rescale=False,
+            n_autos=3):
+    F, ld = llr.shape
+    p = B.params(iters, alpha, n_autos=n_autos, early_stop=early_stop, msg=msg, rescale=rescale)
+    d_llr = to_dev(llr)
+    d_aut = autos_dev(autos) if autos is not None else None
+    hard = torch.zeros((F, W64(c.n)), dtype=torch.int64, device="cuda")
+    it = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    fl = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    yo = torch.full((F, ld), 7.0, dtype=torch.float32, device="cuda")
+    B.nms_decode(c, p, d_llr, d_aut, hard, it, fl, yo)
+    torch.cuda.synchronize()
+    return dict(hard=B.unpack_bits(hard.cpu().numpy(), c.n), iters=it.cpu().numpy(),
+                flags=fl.cpu().numpy(), y=yo.cpu().numpy())
+
+
+# ------------------------------------------------------------------ draws and frames
+@pytest.mark.parametrize("n,P", [(63, 3), (127, 3), (127, 9), (15, 3)])
+def test_autos_device_bit_exact(torch_cuda, n, P):
+    torch = torch_cuda
+    F = 10007
+    out = torch.zeros((F, P), dtype=torch.int16, device="cuda")
+    B.draw_automorphisms(n, P, 99, 123, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint16), O.draw_autos(n, P, 99, 123, F))
+
+
+@pytest.mark.parametrize("nk,ld,lo,hi", [((63, 36), 64, 3.0, 3.0), ((127, 64), 128, 2.0, 5.0),
+                                         ((63, 45), 63, 1.0, 6.0), ((15, 7), 16, 4.0, 4.0)])
+def test_framegen_matches_oracle(torch_cuda, nk, ld, lo, hi):
+    torch = torch_cuda
+    n, k = nk
+    F = 3001
+    c = code(n, k)
+    llr = torch.full((F, ld), 5.0, dtype=torch.float32, device="cuda")
+    cw = torch.zeros((F, W64(n)), dtype=torch.int64, device="cuda")
+    B.gen_frames(c, lo, hi, 77, 1000, llr, cw)
+    torch.cuda.synchronize()
+    ref_llr, ref_cw, ref_e = O.framegen(n, k, 77, 1000, F, lo, hi, ld=ld)
+    assert np.array_equal(B.unpack_bits(cw.cpu().numpy(), n), ref_cw)
+    got = llr.cpu().numpy()
+    scale = np.array([2.0 / O.sigma2(n, k, e) for e in ref_e])[:, None]
+    tol = 1e-5 * np.maximum(np.abs(ref_llr), scale)
+    assert np.all(np.abs(got - ref_llr) <= tol)
+    assert np.all(got[:, n:] == 0)
+
+
+# ------------------------------------------------------------------ enhanced NMS
+@pytest.mark.parametrize("nk", CODES)
+def test_enhanced_one_iteration(torch_cuda, nk):
+    n, k = nk
+    c = code(n, k)
+    F = 1000  # not a multiple of the warp or block size
+    cw, llr = frames(n, k, F, 2.0, 100 + n + k, ld=(n + 3) & ~3)
+    autos = O.draw_autos(n, 3, 5, 0, F)
+    g = run_nms(torch_cuda, c, llr, autos, 1, 0.78, early_stop=False)
+    ref = O.nms_enhanced(c.dense(), llr, autos, 1, 0.78, early_stop=False, trace=True)
+    ok = rel_close(g["y"][:, :n], ref["y"], ref["mag"][:, 0, :])
+    assert ok.all(), f"{(~ok).sum()} entries out of tolerance"
+    assert np.all(g["y"][:, n:] == 7.0)  # padding columns untouched
+    assert np.all(g["iters"] == 1)
+
+
+@pytest.mark.parametrize("nk", CODES)
+@pytest.mark.parametrize("ebn0", [1.5, 3.5])
+def test_enhanced_full_decode(torch_cuda, nk, ebn0):
+    n, k = nk
+    c = code(n, k)
+    F = 1500
+    cw, llr = frames(n, k, F, ebn0, 200 + n + k, ld=(n + 3) & ~3)
+    autos = O.draw_autos(n, 3, 11, 0, F)
+    alpha = np.linspace(0.7, 0.9, 12)
+    g = run_nms(torch_cuda, c, llr, autos, 12, alpha)
+    ref = O.nms_enhanced(c.dense(), llr, autos, 12, alpha, trace=True, threads=None)
+    amb = ambiguous_frames(llr, ref, n)
+    assert amb.mean() < 0.05
+    ok = ~amb
+    assert np.array_equal(g["iters"][ok], ref["iters"][ok])
+    assert np.array_equal(g["hard"][ok], ref["hard"][ok])
+    assert np.array_equal(g["flags"][ok] & 1, ref["converged"][ok])
+    last = np.maximum(ref["iters"] - 1, 0)
+    mag = ref["mag"][np.arange(F), last]
+    close = rel_close(g["y"][:, :n], ref["y"], mag)
+    assert close[ok].all()
+
+
+def test_enhanced_nine_automorphisms_and_unaligned_ld(torch_cuda):
+    n, k = 63, 45
+    c = code(n, k)
+    F = 333
+    cw, llr = frames(n, k, F, 2.5, 300, ld=n)  # ld = 63: scalar load path
+    autos = O.draw_autos(n, 9, 3, 0, F)
+    g = run_nms(torch_cuda, c, llr, autos, 6, 0.8, n_autos=9)
+    ref = O.nms_enhanced(c.dense(), llr, autos, 6, 0.8, trace=True)
+    ok = ~ambiguous_frames(llr, ref, n)
+    assert np.array_equal(g["hard"][ok], ref["hard"][ok])
+    assert np.array_equal(g["iters"][ok], ref["iters"][ok])
+
+
+def test_enhanced_noiseless_one_iteration(torch_cuda):
+    for n, k in CODES:
+        c = code(n, k)
+        cw = O.encode(n, k, np.random.default_rng(n).integers(0, 2, (77, k), dtype=np.uint8))
+        llr = (3.0 * (1 - 2.0 * cw)).astype(np.float32)
+        g = run_nms(torch_cuda, c, llr, O.draw_autos(n, 3, 1, 0, 77), 12, 0.78)
+        assert np.all(g["iters"] == 1) and np.all(g["flags"] & 1)
+        assert np.array_equal(g["hard"], cw)
+
+
+def test_zero_frames_is_noop(torch_cuda):
+    torch = torch_cuda
+    c = code(63, 45)
+    p = B.params(12, 0.78)
+    empty = torch.zeros((0, 64), dtype=torch.float32, device="cuda")
+    hard = torch.zeros((0, 1), dtype=torch.int64, device="cuda")
+    B.nms_decode(c, p, empty, torch.zeros((0, 3), dtype=torch.int16, device="cuda"), hard)
+    torch.cuda.synchronize()
+
+
+def test_invalid_arguments_rejected(torch_cuda):
+    torch = torch_cuda
+    c = code(63, 45)
+    llr = torch.zeros((4, 64), dtype=torch.float32, device="cuda")
+    hard = torch.zeros((4, 1), dtype=torch.int64, device="cuda")
+    with pytest.raises(B.BchError) as e:
+        B.nms_decode(c, B.params(33, 0.78), llr, None, hard)
+    assert e.value.status == B.EINVAL
+    with pytest.raises(B.BchError):
+        B.nms_decode(c, B.params(12, 0.78, n_autos=3), llr, None, hard)  # autos missing
+    with pytest.raises(B.BchError):
+        B.nms_decode(c, B.params(12, 0.78), llr[:, :32].contiguous(), None, hard)  # ld < n
+
+
+def test_batch_independence(torch_cuda):
+    # a frame decodes to the same bits whatever batch it is in (persistent scheduling)
+    n, k = 127, 64
+    c = code(n, k)
+    F = 700
+    _, llr = frames(n, k, F, 2.0, 400, ld=128)
+    autos = O.draw_autos(n, 3, 2, 0, F)
+    full = run_nms(torch_cuda, c, llr, autos, 12, 0.78)
+    part = run_nms(torch_cuda, c, llr[350:400], autos[350:400], 12, 0.78)
+    assert np.array_equal(full["hard"][350:400], part["hard"])
+    assert np.array_equal(full["y"][350:400], part["y"])
+
+
+# ------------------------------------------------------------------ plain NMS
+@pytest.mark.parametrize("ebn0", [2.0, 3.0])
+def test_plain_nms_standard_h(torch_cuda, ebn0):
+    n, k = 63, 36
+    c = code(n, k, B.PCM_STANDARD)
+    F = 1200
+    cw, llr = frames(n, k, F, ebn0, 500, ld=64)
+    g = run_nms(torch_cuda, c, llr, None, 8, 0.78, n_autos=0)
+    ref = O.nms_plain(c.dense(), llr, 8, 0.78, threads=None)
+    amb = np.any(np.abs(llr[:, :n]) < 1e-3, axis=1) | (np.abs(ref["y"]) < 1e-3).any(1)
+    ok = ~amb
+    assert np.array_equal(g["iters"][ok], ref["iters"][ok])
+    agree = np.all(g["hard"] == ref["hard"], axis=1)
+    assert agree[ok].mean() > 0.995
+    close = rel_close(g["y"][:, :n], ref["y"], np.abs(ref["y"]) + np.abs(llr[:, :n]) * 0 + 1.0)
+    assert close[ok & agree].mean() > 0.99
+
+
+# ------------------------------------------------------------------ OSD and hybrid
+@pytest.mark.parametrize("nk", [(15, 7), (63, 36), (63, 45), (127, 64), (127, 99)])
+def test_osd_order2_bit_exact(torch_cuda, nk):
+    torch = torch_cuda
+    n, k = nk
+    std = code(n, k, B.PCM_STANDARD)
+    F = 150 if n == 127 else 400
+    cw, llr = frames(n, k, F, 1.5, 600 + n + k, ld=(n + 3) & ~3)
+    d_llr = to_dev(llr)
+    lst = torch.arange(F, dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([F], dtype=torch.int32, device="cuda")
+    hard = torch.zeros((F, W64(n)), dtype=torch.int64, device="cuda")
+    fl = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    B.osd_decode(std, 2, d_llr, lst, cnt, hard, fl)
+    torch.cuda.synchronize()
+    ref, _ = O.osd(std.dense(), llr, order=2, threads=None)
+    assert np.array_equal(B.unpack_bits(hard.cpu().numpy(), n), ref)
+    assert np.all(fl.cpu().numpy() == B.FLAG_OSD)
+
+
+def test_osd_partial_list(torch_cuda):
+    torch = torch_cuda
+    n, k = 63, 45
+    std = code(n, k, B.PCM_STANDARD)
+    F = 100
+    cw, llr = frames(n, k, F, 2.0, 650, ld=64)
+    sel = np.array([3, 17, 50, 99], np.int32)
+    hard = torch.full((F, 1), -1, dtype=torch.int64, device="cuda")
+    B.osd_decode(std, 1, to_dev(llr), to_dev(sel), to_dev(np.array([4], np.int32)), hard)
+    torch.cuda.synchronize()
+    h = hard.cpu().numpy()
+    ref, _ = O.osd(std.dense(), llr[sel], order=1)
+    assert np.array_equal(B.unpack_bits(h[sel], n), ref)
+    others = np.setdiff1d(np.arange(F), sel)
+    assert np.all(h[others] == -1)
+
+
+@pytest.mark.parametrize("nk,ebn0", [((127, 99), 3.0), ((127, 64), 2.5), ((63, 36), 2.0),
+                                     ((15, 7), 2.0)])
+def test_hybrid_matches_oracle(torch_cuda, nk, ebn0):
+    torch = torch_cuda
+    n, k = nk
+    c, std = code(n, k), code(n, k, B.PCM_STANDARD)
+    F = 600
+    cw, llr = frames(n, k, F, ebn0, 700 + n + k, ld=(n + 3) & ~3)
+    autos = O.draw_autos(n, 3, 13, 0, F)
+    p = B.params(12, 0.78, osd_order=2)
+    hard = torch.zeros((F, W64(n)), dtype=torch.int64, device="cuda")
+    it = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    fl = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    lst = torch.zeros(F, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.hybrid_decode(c, std, p, to_dev(llr), autos_dev(autos), hard, it, fl, failed_list=lst,
+                    failed_count=cnt)
+    torch.cuda.synchronize()
+    ref = O.hybrid(c.dense(), std.dense(), llr, autos, 12, 0.78, threads=None)
+    refe = O.nms_enhanced(c.dense(), llr, autos, 12, 0.78, trace=True, threads=None)
+    ok = ~ambiguous_frames(llr, refe, n)
+    got = B.unpack_bits(hard.cpu().numpy(), n)
+    assert np.array_equal(got[ok], ref["final"][ok])
+    flags = fl.cpu().numpy()
+    osd_frames = np.nonzero(flags & B.FLAG_OSD)[0]
+    fails = np.nonzero((flags & B.FLAG_CONVERGED) == 0)[0]
+    assert np.array_equal(osd_frames, fails)
+    nf = int(cnt.cpu().numpy()[0])
+    assert nf == fails.size
+    assert np.array_equal(lst.cpu().numpy()[:nf], fails)  # ascending frame order
+    # OSD output is a codeword
+    H = std.dense()
+    assert np.all((got[osd_frames].astype(np.int64) @ H.T) % 2 == 0)
+
+
+def test_count_errors(torch_cuda):
+    torch = torch_cuda
+    n = 127
+    rng = np.random.default_rng(5)
+    F = 5000
+    a = rng.integers(0, 2, (F, n), dtype=np.uint8)
+    b = a.copy()
+    flip = rng.random((F, n)) < 0.002
+    b[flip] ^= 1
+    it = rng.integers(1, 13, F).astype(np.uint8)
+    fl = rng.integers(0, 4, F).astype(np.uint8)
+    ctr = torch.zeros(8, dtype=torch.int64, device="cuda")
+    B.count_errors(n, to_dev(B.pack_bits(b)), to_dev(B.pack_bits(a)), to_dev(it), to_dev(fl), ctr)
+    torch.cuda.synchronize()
+    got = ctr.cpu().numpy()
+    fe = flip.any(1)
+    assert got[0] == F and got[1] == fe.sum() and got[2] == flip.sum()
+    assert got[3] == (fe & ((fl & 1) == 1) & ((fl & 2) == 0)).sum()
+    assert got[4] == ((fl & 2) > 0).sum() and got[5] == it.sum() and got[6] == (fl & 1).sum()

@@ -1,0 +1,75 @@
+"""GPU parity of the training path: checkpointed forward pass, the hand-written
+backward kernel (subgradient through min1/min2) and the BCE loss, against the FP64
+oracle gradient (itself pinned by central finite differences)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import autos_dev, frames, rel_close, to_dev
+from paper_2412_20828_gb300 import bchdec as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2412_20828_gb300 import build
+    build.build()
+    B.load()
+    return torch
+
+
+@pytest.mark.parametrize("nk", [(63, 45), (127, 64)])
+def test_forward_checkpoints_and_backward(torch_cuda, nk):
+    torch = torch_cuda
+    n, k = nk
+    c = B.Code(n, k)
+    Ho = c.dense()
+    I = 4
+    alpha = np.array([0.7, 0.75, 0.8, 0.85])
+    F0 = 256
+    cw, llr = frames(n, k, F0, 3.0, 800 + n, ld=(n + 3) & ~3)
+    autos = O.draw_autos(n, 3, 21, 0, F0)
+    # keep frames whose subgradient is unique (no near-tie of the two smallest |z|)
+    _, _, _, _, tm = O.train_grad(Ho, llr, autos, I, alpha, cw, return_margin=True)
+    sel = np.nonzero(tm > 1e-3)[0][:96]
+    assert sel.size >= 48
+    cw, llr, autos = cw[sel], np.ascontiguousarray(llr[sel]), np.ascontiguousarray(autos[sel])
+    F, ld = llr.shape
+    loss_ref, da_ref, dl_ref, y_ref = O.train_grad(Ho, llr, autos, I, alpha, cw)
+    p = B.params(I, alpha, n_autos=3, early_stop=False)
+    d_llr, d_aut = to_dev(llr), autos_dev(autos)
+    ckpt = torch.zeros((I + 1, F, ld), dtype=torch.float32, device="cuda")
+    ws = B.workspace(c, p, F)
+    B.nms_forward_train(c, p, d_llr, d_aut, ckpt, ws)
+    # checkpoints against the oracle trace
+    tr = O.nms_enhanced(Ho, llr, autos, I, alpha, early_stop=False, trace=True)
+    ck = ckpt.cpu().numpy()
+    for t in range(I + 1):
+        mag = tr["mag"][:, t - 1, :] if t > 0 else None
+        assert rel_close(ck[t, :, :n], tr["trace"][:, t, :], mag).all(), t
+    # loss and its gradient
+    d_cw = to_dev(B.pack_bits(cw))
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gout = torch.zeros((F, ld), dtype=torch.float32, device="cuda")
+    B.bce_loss(n, ckpt[I], d_cw, loss, gout, ws)
+    torch.cuda.synchronize()
+    assert float(loss.cpu()[0]) == pytest.approx(loss_ref, rel=1e-4)
+    # backward
+    gl = torch.zeros((F, ld), dtype=torch.float32, device="cuda")
+    ga = torch.zeros(I, dtype=torch.float32, device="cuda")
+    B.nms_backward(c, p, d_aut, ckpt, gout, gl, ga, ws)
+    torch.cuda.synchronize()
+    assert np.allclose(ga.cpu().numpy(), da_ref, rtol=2e-3, atol=1e-6 * np.abs(da_ref).max())
+    g = gl.cpu().numpy()[:, :n]
+    scale = np.abs(dl_ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(g - dl_ref) <= 1e-3 * scale + 1e-12)
+
+
+def test_train_alpha_reduces_loss(torch_cuda):
+    c = B.Code(63, 45)
+    alpha, hist = B.train_alpha(c, 3, 6, np.full(6, 0.5), steps=30, batch=4096, ebn0_lo=2.0,
+                                ebn0_hi=5.0, seed=3, lr=0.02)
+    assert np.all(np.isfinite(alpha)) and np.all(np.isfinite(hist))
+    assert hist[-5:].mean() < hist[:5].mean()
