@@ -108,6 +108,16 @@ bch_status bch_build_pcm_host(int n, int k, bch_pcm_kind kind, int m_rows, uint6
                               const bch_pcm_opts *opts, uint8_t *dense, size_t capacity,
                               int *rows);
 
+/* Names the enhanced-NMS kernel a decode of `code` with storage `msg` and n_autos
+ * automorphisms runs: "jit" -- the kernel compiled at run time (NVRTC) for this code's
+ * Tanner graph, rows as straight-line code on registers -- or "generic: <reason>" --
+ * the precompiled kernel that reads the rows from shared memory.  The environment
+ * variable BCHDEC_NMS_KERNEL=generic|jit|auto selects (default auto: jit for n <= 63
+ * when it compiles, generic for n = 127).  The first call for a code compiles (a few
+ * seconds) and caches the kernel; BCHDEC_JIT_MIN_BLOCKS sets its register budget. */
+bch_status bch_nms_kernel_info(const bch_code *code, int msg, int n_autos, char *buf,
+                               size_t capacity);
+
 /* Dimensions of a code object: n, k, rows, edges (ones in the matrix), max row weight. */
 bch_status bch_code_info(const bch_code *code, int *n, int *k, int *rows, int *edges,
                          int *max_row_weight);

@@ -66,9 +66,11 @@ def _load():
             "or_framegen": (i, [i, i, u64, u64, i, d, d, P, i, P, P]),
             "or_draw_autos": (i, [i, i, u64, u64, i, P]),
             "or_build_ho": (i, [i, i, i, u64, i, i, d, d, d, P, P, P]),
-            "or_nms_plain": (i, [P, i, i, P, i, i, i, d, i, P, P, P, P]),
+            "or_nms_plain": (i, [P, i, i, P, i, i, i, d, i, P, P, P, P, P, P]),
             "or_nms_enhanced": (i, [P, i, i, P, i, i, i, P, i, P, i, P, P, P, P, P, P, P]),
             "or_osd": (i, [P, i, i, P, i, i, i, P, P, P]),
+            "or_q16": (d, [d]),
+            "or_nms_enhanced_q": (i, [P, i, i, P, i, i, i, P, i, P, i, i, i, P, P, P, P]),
             "or_ml": (i, [i, i, P, i, i, P]),
             "or_nms_train_grad": (i, [P, i, i, P, i, i, i, P, i, P, P, P, P, P, P, P]),
         }
@@ -219,15 +221,17 @@ def nms_plain(H, llr, iters, alpha, early_stop=True, threads=1):
     it = np.zeros(F, np.int32)
     conv = np.zeros(F, np.uint8)
     y = np.zeros((F, n), np.float64)
+    env = np.zeros(F, np.float64)
+    mar = np.zeros(F, np.float64)
     lib = _load()
 
     def run(a, b):
         _check(lib.or_nms_plain(_p(H), M, n, _p(llr[a:]), ld, b - a, iters, float(alpha),
                                 int(early_stop), _p(hard[a:]), _p(it[a:]), _p(conv[a:]),
-                                _p(y[a:])), "nms_plain")
+                                _p(y[a:]), _p(env[a:]), _p(mar[a:])), "nms_plain")
 
     _pool_map(run, F, 256, threads)
-    return dict(hard=hard, iters=it, converged=conv, y=y)
+    return dict(hard=hard, iters=it, converged=conv, y=y, env=env, margin_rel=mar)
 
 
 def nms_enhanced(Ho, llr, autos, iters, alpha, early_stop=True, trace=False, threads=1):
@@ -262,6 +266,34 @@ def nms_enhanced(Ho, llr, autos, iters, alpha, early_stop=True, trace=False, thr
         out["trace"] = tr
         out["mag"] = mag
     return out
+
+
+def q16(x: float) -> float:
+    return _load().or_q16(float(x))
+
+
+def nms_enhanced_q(Ho, llr, autos, iters, alpha, fmt, rescale=False, early_stop=True, threads=1):
+    """Algorithm 1 with FP16 (fmt=1) or 8-bit (fmt=2) storage; see the C header."""
+    Ho = np.ascontiguousarray(Ho, np.uint8)
+    M, n = Ho.shape
+    llr = np.ascontiguousarray(llr, np.float32)
+    F, ld = llr.shape
+    autos = np.ascontiguousarray(autos, np.uint16).reshape(F, -1)
+    P = autos.shape[1]
+    al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float64), (iters,)))
+    hard = np.zeros((F, n), np.uint8)
+    it = np.zeros(F, np.int32)
+    conv = np.zeros(F, np.uint8)
+    y = np.zeros((F, n), np.float64)
+    lib = _load()
+
+    def run(a, b):
+        _check(lib.or_nms_enhanced_q(_p(Ho), M, n, _p(llr[a:]), ld, b - a, P, _p(autos[a:]), iters,
+                                     _p(al), int(early_stop), fmt, int(rescale), _p(hard[a:]),
+                                     _p(it[a:]), _p(conv[a:]), _p(y[a:])), "nms_enhanced_q")
+
+    _pool_map(run, F, 256, threads)
+    return dict(hard=hard, iters=it, converged=conv, y=y)
 
 
 def osd(H, llr, order=2, threads=1, return_mrb=False):

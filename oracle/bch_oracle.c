@@ -33,6 +33,9 @@
  *                                     generator-side basis.
  *   or_ml                             pinned: corrects every <= t error pattern.
  *   or_nms_train_grad                 pinned: central finite differences.
+ *   or_nms_enhanced_q, or_q16         pinned: binary16 rounding against numpy's
+ *                                     float16; quantised decode equals the FP64 decode
+ *                                     on inputs that are exact in the format.
  *   or_philox4x32_10                  pinned: published known-answer vectors.
  *   or_splitmix64                     pinned: published first output.
  */
@@ -818,10 +821,11 @@ static int row_vars(const uint8_t *H, int n, int r, int *vars) {
  * (Eq. 4 read with the latest messages, otherwise iteration 1 could never change a
  * decision); hard decision c_i = [x_i < 0]; stop when H c^T = 0 (if early_stop) or
  * after `iters` iterations.  Outputs per frame: hard bits (bytes), iterations run,
- * converged flag, final x (double). */
+ * converged flag, final x (double), the largest operand magnitude met (|L| + sum of
+ * |c2v| over a variable's edges) and the smallest |v2c| or |x| relative to it. */
 int or_nms_plain(const uint8_t *H, int M, int n, const float *llr, int ld, int F, int iters,
                  double alpha, int early_stop, uint8_t *hard, int *iters_used,
-                 uint8_t *converged, double *y_out) {
+                 uint8_t *converged, double *y_out, double *env_out, double *margin_out) {
   double *c2v = (double *)calloc((size_t)M * n, sizeof(double));
   double *nc2v = (double *)calloc((size_t)M * n, sizeof(double));
   double *v2c = (double *)calloc((size_t)M * n, sizeof(double));
@@ -833,9 +837,11 @@ int or_nms_plain(const uint8_t *H, int M, int n, const float *llr, int ld, int F
     const float *L = llr + (size_t)f * ld;
     memset(c2v, 0, sizeof(double) * (size_t)M * n);
     int t_run = 0, ok = 0;
+    double env = 0.0, mar = INFINITY;
     for (int i = 0; i < n; i++) {
       x[i] = (double)L[i];
       c[i] = x[i] < 0.0;
+      if (fabs(x[i]) > env) env = fabs(x[i]);
     }
     for (int t = 1; t <= iters; t++) {
       /* Eq. (2) */
@@ -855,13 +861,21 @@ int or_nms_plain(const uint8_t *H, int M, int n, const float *llr, int ld, int F
       }
       memcpy(c2v, nc2v, sizeof(double) * (size_t)M * n);
       /* Eq. (4) */
+      double tmar = INFINITY;
       for (int i = 0; i < n; i++) {
-        double s = (double)L[i];
+        double s = (double)L[i], sa = fabs((double)L[i]);
         for (int j = 0; j < M; j++)
-          if (H[j * n + i]) s += c2v[j * n + i];
+          if (H[j * n + i]) {
+            s += c2v[j * n + i];
+            sa += fabs(c2v[j * n + i]);
+            if (fabs(v2c[j * n + i]) < tmar) tmar = fabs(v2c[j * n + i]);
+          }
         x[i] = s;
         c[i] = s < 0.0;
+        if (sa > env) env = sa;
+        if (fabs(s) < tmar) tmar = fabs(s);
       }
+      if (tmar / env < mar) mar = tmar / env;
       t_run = t;
       ok = or_syndrome_weight(H, M, n, c) == 0;
       if (early_stop && ok) break;
@@ -870,6 +884,8 @@ int or_nms_plain(const uint8_t *H, int M, int n, const float *llr, int ld, int F
     if (iters_used) iters_used[f] = t_run;
     if (converged) converged[f] = (uint8_t)ok;
     if (y_out) memcpy(y_out + (size_t)f * n, x, sizeof(double) * (size_t)n);
+    if (env_out) env_out[f] = env;
+    if (margin_out) margin_out[f] = mar;
   }
   free(c2v); free(nc2v); free(v2c); free(vars);
   return OR_OK;
@@ -968,6 +984,112 @@ int or_nms_enhanced(const uint8_t *Ho, int M, int n, const float *llr, int ld, i
     if (converged) converged[f] = (uint8_t)ok;
     if (y_out) memcpy(y_out + (size_t)f * n, y, sizeof(double) * (size_t)n);
     if (margin) margin[f] = mar;
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------
+ * Reduced-precision storage of the enhanced decoder (the library's FP16 and 8-bit
+ * message formats), restated with the quantisers applied at the same points:
+ *   FP16: y stored as binary16 (round to nearest even, saturating at +-65504); each
+ *         check-to-variable magnitude alpha_t * min rounded to binary16; sums and the
+ *         merge exact (double).
+ *   INT8: y stored as q = clamp(rne(4x), -31, 31) (LSB = 1/4); minima and signs on q;
+ *         check-to-variable magnitude rne(alpha_t * min_q) (integer); merge
+ *         q + (sum of c2v) / P exact, then re-quantised.
+ * rescale = 1: after each merge the frame is divided by the smallest power of two
+ * bringing max |y| to <= 16384 (FP16) or <= 31 (INT8); hard decisions are taken on
+ * the merged value before the division.  y_out returns the value in LLR units.
+ * ---------------------------------------------------------------------------- */
+double or_q16(double x) {
+  double a = fabs(x);
+  if (a == 0.0) return 0.0;
+  if (a >= 65504.0) return x < 0 ? -65504.0 : 65504.0;
+  int E;
+  frexp(a, &E); /* a = f 2^E, f in [0.5, 1): leading bit 2^(E-1) */
+  double quantum = (E - 1 < -14) ? ldexp(1.0, -24) : ldexp(1.0, E - 1 - 10);
+  double r = rint(a / quantum) * quantum;
+  if (r > 65504.0) r = 65504.0;
+  return x < 0 ? -r : r;
+}
+
+static double q8(double x) {
+  double r = rint(x);
+  if (r > 31.0) r = 31.0;
+  if (r < -31.0) r = -31.0;
+  return r;
+}
+
+int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld, int F, int P,
+                      const uint16_t *autos, int iters, const double *alpha, int early_stop,
+                      int fmt, int rescale, uint8_t *hard, int *iters_used, uint8_t *converged,
+                      double *y_out) {
+  if (fmt != 1 && fmt != 2) return OR_EARG;
+  double y[128], yn[128], z[128], S[128], sum[128], rowbuf[128];
+  int vars[128], pi[128];
+  uint8_t c[128];
+  const double lim = fmt == 1 ? 16384.0 : 31.0;
+  for (int f = 0; f < F; f++) {
+    const float *L = llr + (size_t)f * ld;
+    const uint16_t *aut = autos + (size_t)f * P;
+    int escale = 0;
+    for (int i = 0; i < n; i++) {
+      double x = (double)L[i];
+      y[i] = fmt == 1 ? or_q16(x) : q8(4.0 * x);
+      c[i] = x < 0.0;
+    }
+    int t_run = 0, ok = 0;
+    for (int t = 1; t <= iters; t++) {
+      for (int i = 0; i < n; i++) sum[i] = 0.0;
+      for (int p = 0; p < P; p++) {
+        for (int i = 0; i < n; i++) {
+          pi[i] = auto_apply(aut[p], n, i);
+          z[pi[i]] = y[i];
+        }
+        for (int u = 0; u < n; u++) S[u] = 0.0;
+        for (int j = 0; j < M; j++) {
+          int w = row_vars(Ho, n, j, vars);
+          for (int e = 0; e < w; e++) rowbuf[e] = z[vars[e]];
+          for (int e = 0; e < w; e++) {
+            double sg = 1.0, mn = INFINITY;
+            for (int e2 = 0; e2 < w; e2++) {
+              if (e2 == e) continue;
+              if (rowbuf[e2] < 0.0) sg = -sg;
+              if (fabs(rowbuf[e2]) < mn) mn = fabs(rowbuf[e2]);
+            }
+            double mag = alpha[t - 1] * mn;
+            mag = fmt == 1 ? or_q16(mag) : rint(mag);
+            S[vars[e]] += sg * mag;
+          }
+        }
+        for (int i = 0; i < n; i++) sum[i] += S[pi[i]];
+      }
+      double mx = 0.0;
+      for (int i = 0; i < n; i++) {
+        yn[i] = y[i] + sum[i] / (double)P;
+        c[i] = yn[i] < 0.0;
+        if (fabs(yn[i]) > mx) mx = fabs(yn[i]);
+      }
+      double sc = 1.0;
+      if (rescale) {
+        int k = 0;
+        while (mx * sc > lim && k < 126) {
+          sc *= 0.5;
+          k++;
+        }
+        escale += k;
+      }
+      for (int i = 0; i < n; i++) y[i] = fmt == 1 ? or_q16(yn[i] * sc) : q8(yn[i] * sc);
+      t_run = t;
+      ok = or_syndrome_weight(Ho, M, n, c) == 0;
+      if (early_stop && ok) break;
+    }
+    if (hard) memcpy(hard + (size_t)f * n, c, (size_t)n);
+    if (iters_used) iters_used[f] = t_run;
+    if (converged) converged[f] = (uint8_t)ok;
+    if (y_out)
+      for (int i = 0; i < n; i++)
+        y_out[(size_t)f * n + i] = ldexp(fmt == 1 ? y[i] : y[i] / 4.0, escale);
   }
   return OR_OK;
 }
@@ -1117,8 +1239,8 @@ int or_ml(int n, int k, const float *llr, int ld, int F, uint8_t *cw_out) {
  *                            (lowest column on ties); sign derivatives are zero;
  *   the dilation, un-permutation and average are linear.
  * Outputs: loss, dL/dalpha [iters], dL/dLLR [F][n], final y [F][n], and per frame the
- * smallest gap, relative to the row's largest |z|, between a row's two smallest |z|
- * or between the smallest |z| and zero (where the subgradient is not unique).
+ * smallest relative gap (s2 - s1) / s2 between a row's two smallest |z| (where the
+ * subgradient is not unique when the gap is zero).
  * ---------------------------------------------------------------------------- */
 int or_nms_train_grad(const uint8_t *Ho, int M, int n, const float *llr, int ld, int F, int P,
                       const uint16_t *autos, int iters, const double *alpha, const uint8_t *cw,
@@ -1176,10 +1298,8 @@ int or_nms_train_grad(const uint8_t *Ho, int M, int n, const float *llr, int ld,
             if (a < s1) { s2 = s1; s1 = a; } else if (a < s2) s2 = a;
           }
           {
-            double g1 = (s2 - s1) / (sc > 1.0 ? sc : 1.0);
-            double g0 = s1 / (sc > 1.0 ? sc : 1.0);
+            double g1 = s2 > 0.0 ? (s2 - s1) / s2 : 0.0;
             if (g1 < tm) tm = g1;
-            if (g0 < tm) tm = g0;
           }
           for (int e = 0; e < w; e++) {
             double sg = 1.0, mn = INFINITY;

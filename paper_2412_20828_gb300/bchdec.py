@@ -23,7 +23,7 @@ FLAG_CONVERGED, FLAG_OSD = 1, 2
 
 # Every symbol the header declares (checked by the tests without a GPU).
 EXPORTS = (
-    "bch_build_pcm", "bch_build_pcm_host", "bch_code_info", "bch_pcm_export", "bch_code_free",
+    "bch_build_pcm", "bch_build_pcm_host", "bch_nms_kernel_info", "bch_code_info", "bch_pcm_export", "bch_code_free",
     "bch_draw_automorphisms", "bch_draw_automorphisms_host", "bch_gen_frames",
     "bch_workspace_size", "bch_nms_decode", "bch_hybrid_decode", "bch_osd_decode",
     "bch_compact_failed", "bch_count_errors", "bch_nms_forward_train", "bch_nms_backward", "bch_bce_loss",
@@ -69,6 +69,7 @@ def load():
         sig = {
             "bch_build_pcm": (st, [i, i, i, i, u64, C.POINTER(PcmOpts), C.POINTER(P)]),
             "bch_build_pcm_host": (st, [i, i, i, i, u64, C.POINTER(PcmOpts), P, sz, C.POINTER(i)]),
+            "bch_nms_kernel_info": (st, [P, i, i, C.c_char_p, sz]),
             "bch_code_info": (st, [P, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i),
                                    C.POINTER(i)]),
             "bch_pcm_export": (st, [P, P, sz]),
@@ -155,6 +156,11 @@ class Code:
     @property
     def handle(self):
         return self._h
+
+    def kernel_info(self, msg=MSG_FP32, n_autos=3) -> str:
+        buf = C.create_string_buffer(4096)
+        _check(load().bch_nms_kernel_info(self._h, msg, n_autos, buf, 4096), "bch_nms_kernel_info")
+        return buf.value.decode()
 
     def dense(self) -> np.ndarray:
         out = np.zeros((self.rows, self.n), np.uint8)

@@ -20,8 +20,9 @@ INCLUDE = os.path.join(ROOT, "include")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["k_nms.cu", "k_osd.cu", "k_misc.cu", "k_train.cu", "capi.cu", "runtime.cu"]
-CPP_SOURCES = ["bch_host.cpp"]
+CU_SOURCES = ["k_nms.cu", "k_nms_fp32.cu", "k_nms_fp16.cu", "k_nms_int8.cu", "k_osd.cu", "k_misc.cu",
+              "k_train.cu", "capi.cu", "runtime.cu"]
+CPP_SOURCES = ["bch_host.cpp", "jit.cpp"]
 
 
 def _deps_mtime() -> float:
@@ -38,6 +39,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
     inc = ["-I", CSRC, "-I", INCLUDE]
     procs = []
     objs = []
+    # the device headers the run-time compiler needs, embedded as text
+    gen = os.path.join(OUT, "gen_device_text.cpp")
+    with open(gen, "w") as f:
+        f.write("namespace bchlib {\n")
+        for sym, name in (("kDevTypesText", "bch_devtypes.h"), ("kNmsDeviceText", "nms_device.cuh")):
+            with open(os.path.join(CSRC, name)) as g:
+                text = g.read()
+            assert ")__BCHTEXT__" not in text
+            f.write(f'extern const char {sym}[] = R"__BCHTEXT__({text})__BCHTEXT__";\n')
+        f.write("}  // namespace bchlib\n")
+    gobj = gen + ".o"
+    procs.append(("gen_device_text.cpp", subprocess.Popen(
+        ["g++", "-O1", "-std=c++17", "-fPIC", "-c", gen, "-o", gobj],
+        stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    objs.append(gobj)
     for src in CU_SOURCES:
         obj = os.path.join(OUT, src + ".o")
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -7,22 +7,6 @@
 
 namespace bchlib {
 
-struct NmsArgs {
-  DevCode dc;
-  const float *llr;
-  int ld, F;
-  const uint16_t *autos;
-  int P;
-  uint64_t *hard;
-  uint8_t *iters;
-  uint8_t *flags;
-  float *llr_out;
-  float *ckpt;  // training checkpoints [I+1][F][ld] or null
-  unsigned *queue;
-  int I, early_stop, msg, rescale;
-  float alpha[32];
-};
-
 struct OsdArgs {
   int n, k, M;
   const uint4 *rows;  // [M] standard H rows, 4 x u32

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "bch_devtypes.h"
 #include "bchdec.h"
 
 namespace bchlib {
@@ -66,25 +67,6 @@ int gf2_rank(std::vector<Row> rows, int n);
 uint64_t splitmix64_next(uint64_t *state);
 uint64_t splitmix64_mix(uint64_t z);
 void draw_autos_host(int n, int P, uint64_t seed, uint64_t frame0, int F, uint16_t *out);
-
-// ----------------------------------------------------------------- device layout
-// Layout of a code object on the device (one allocation, 256-byte aligned pieces).
-// Rows are grouped by weight; each group stores its rows' column codes
-// d(u) = u | u << m (so that the Frobenius power j of u, rotr_m(u, j), is the m-bit
-// field of d(u) starting at bit j) contiguously.
-constexpr int kMaxGroups = 16;
-constexpr int kMaxN = 127;
-
-struct DevCode {
-  int n, k, m, rows, edges, max_w, nwords32;
-  int n_groups;
-  int group_w[kMaxGroups];     // row weight of the group
-  int group_rows[kMaxGroups];  // number of rows
-  int group_off[kMaxGroups + 1];  // offset into codes (in entries); [n_groups] = end
-  const uint16_t *codes;       // [edges] column codes, group order
-  const uint32_t *rowmask;     // [rows][4] bit-packed rows (syndrome test)
-  const uint64_t *par;         // [k] parity words (systematic encoder)
-};
 
 }  // namespace bchlib
 

@@ -7,28 +7,10 @@
 
 #include "bch_args.h"
 #include "bch_internal.h"
+#include "nms_device.cuh"
 
 namespace bchlib {
 
-constexpr uint32_t kSign = 0x80000000u;
-constexpr unsigned kFull = 0xffffffffu;
-
-// m-bit field of x starting at bit `pos` (PTX bfe).
-__device__ __forceinline__ uint32_t bfe32(uint32_t x, uint32_t pos, uint32_t len) {
-  uint32_t r;
-  asm("bfe.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(pos), "r"(len));
-  return r;
-}
-
-// (a + b) mod n for a, b in [0, n): min(a + b, a + b - n) in unsigned arithmetic.
-__device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, uint32_t n) {
-  uint32_t x = a + b;
-  return __viaddmin_u32(x, 0u - n, x);
-}
-
-__device__ __forceinline__ float flip_sign(float mag, uint32_t sign_src) {
-  return __uint_as_float(__float_as_uint(mag) ^ (sign_src & kSign));
-}
 
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): two 32x32 multiplies per round,
 // key bumped by the Weyl constants between rounds.
@@ -57,6 +39,5 @@ __device__ __forceinline__ uint64_t splitmix64_mix_d(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 }  // namespace bchlib

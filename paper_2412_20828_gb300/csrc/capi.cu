@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -11,6 +12,25 @@
 #include "bch_kernels.cuh"
 
 using namespace bchlib;
+
+namespace bchlib {
+cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err);
+int jit_block_size(int n);
+int jit_scratch_words(int n);
+size_t nms_table_bytes_host(const DevCode &dc);
+}  // namespace bchlib
+
+// Which enhanced-NMS kernel runs: the run-time specialised one ("jit") when it
+// compiles, else the precompiled one.  BCHDEC_NMS_KERNEL=generic|jit|auto overrides.
+static int kernel_mode() {
+  const char *v = std::getenv("BCHDEC_NMS_KERNEL");
+  if (!v) return 0;
+  if (!std::strcmp(v, "generic")) return 1;
+  if (!std::strcmp(v, "jit")) return 2;
+  return 0;
+}
+
+
 
 namespace bchlib {
 
@@ -278,6 +298,25 @@ bch_status bch_build_pcm(int n, int k, bch_pcm_kind kind, int m_rows, uint64_t s
   return BCH_OK;
 }
 
+bch_status bch_nms_kernel_info(const bch_code *code, int msg, int n_autos, char *buf, size_t capacity) {
+  if (!code_ok(code) || !buf || capacity == 0) return fail(BCH_EINVAL, "bad argument");
+  std::string info;
+  const int mode = kernel_mode();
+  if (n_autos == 0) {
+    info = "generic: plain decoder";
+  } else if (mode == 1) {
+    info = "generic: selected by BCHDEC_NMS_KERNEL";
+  } else if (mode == 0 && code->alg.n > 63) {
+    info = "generic: n = 127 (the specialised kernel is opt-in: BCHDEC_NMS_KERNEL=jit)";
+  } else {
+    std::string err;
+    cudaKernel_t k = jit_kernel(code, msg, &err);
+    info = k ? "jit" : "generic: " + err;
+  }
+  std::snprintf(buf, capacity, "%s", info.c_str());
+  return BCH_OK;
+}
+
 bch_status bch_code_info(const bch_code *c, int *n, int *k, int *rows, int *edges, int *max_w) {
   if (!code_ok(c)) return fail(BCH_EINVAL, "null code");
   if (n) *n = c->alg.n;
@@ -355,6 +394,45 @@ bch_status bch_workspace_size(const bch_code *code, const bch_nms_params *params
   return BCH_OK;
 }
 
+static cudaError_t launch_jit(cudaKernel_t k, const bch_code *code, const NmsArgs &a, cudaStream_t st) {
+  const int n = code->alg.n, tpb = jit_block_size(n), scr = jit_scratch_words(n);
+  const size_t sa = a.msg == BCH_MSG_INT8 ? 4 : 4;
+  const size_t sy = a.msg == BCH_MSG_FP32 ? 4 : (a.msg == BCH_MSG_FP16 ? 2 : 1);
+  const size_t smem = nms_table_bytes_host(code->dc) + 16 +
+                      size_t(tpb) * (size_t(a.P) * 4 + size_t(n) * (sa + sy) + size_t(scr) * sa);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  const void *fn = reinterpret_cast<const void *>(k);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tpb, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = (long long)sms * per_sm;
+  const long long need = (a.F + tpb - 1) / tpb;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  void *args[] = {const_cast<NmsArgs *>(&a)};
+  return cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(unsigned(tpb)), args, smem, st);
+}
+
+static cudaError_t launch_nms_code(const bch_code *code, const NmsArgs &a, cudaStream_t st,
+                                   std::string *why) {
+  const int mode = kernel_mode();
+  // auto: the specialised kernel for n <= 63; for n = 127 its compile time (tens of
+  // seconds) and register spills make the precompiled kernel the default
+  if (a.P > 0 && (mode == 2 || (mode == 0 && code->alg.n <= 63))) {
+    std::string err;
+    cudaKernel_t k = jit_kernel(code, a.msg, &err);
+    if (k) return launch_jit(k, code, a, st);
+    if (why) *why = err;
+    if (mode == 2) return cudaErrorNotSupported;
+  }
+  return launch_nms(a, st);
+}
+
 static bch_status run_nms(const bch_code *code, const bch_nms_params *params, const float *llr, int ld,
                           int n_frames, const uint16_t *autos, uint64_t *hard, uint8_t *iters,
                           uint8_t *flags, float *llr_out, float *ckpt, void *workspace,
@@ -373,7 +451,9 @@ static bch_status run_nms(const bch_code *code, const bch_nms_params *params, co
   BCH_CUDA(cudaMemsetAsync(queue, 0, 16, st), "clear queue");
   NmsArgs a = make_nms_args(code, params, llr, ld, n_frames, autos, hard, iters, flags, llr_out, queue);
   a.ckpt = ckpt;
-  BCH_CUDA(launch_nms(a, st), "nms kernel");
+  std::string why;
+  cudaError_t e = launch_nms_code(code, a, st, &why);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("nms kernel: ") + cudaGetErrorString(e) + " " + why);
   return BCH_OK;
 }
 

@@ -1,0 +1,234 @@
+// Run-time specialisation of the enhanced min-sum kernel to one code's Tanner graph.
+//
+// The row loops of the precompiled kernel read column codes from shared memory and
+// gather / scatter through per-frame permuted addresses for every edge.  Here the
+// code's rows are emitted as straight-line CUDA source with the column indices as
+// compile-time constants, so for one automorphism a thread first gathers the permuted
+// word z_p[u] = y[pi_p^-1(u)] into registers (n loads), runs every check row on
+// registers (min1 / min2 / sign product and the c2v sums S[u] for u in the row, 8
+// lane-ops per edge) and finally scatters S into the frame's accumulator (n
+// read-modify-writes).  For n <= 63 both z and S live in registers; for n = 127 z does
+// and S lives in the thread's shared-memory column at compile-time offsets.
+//
+// Compiled with NVRTC (loaded with dlopen, so the library still loads on machines
+// without it) for sm_103a and loaded with cudaLibraryLoadData; cached per source text.
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "bch_internal.h"
+
+namespace bchlib {
+
+extern const char kDevTypesText[];
+extern const char kNmsDeviceText[];
+
+namespace {
+
+struct NvrtcApi {
+  bool ok = false;
+  std::string err;
+  decltype(&nvrtcCreateProgram) create = nullptr;
+  decltype(&nvrtcCompileProgram) compile = nullptr;
+  decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&nvrtcGetProgramLog) log = nullptr;
+  decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&nvrtcGetCUBIN) cubin = nullptr;
+  decltype(&nvrtcDestroyProgram) destroy = nullptr;
+};
+
+NvrtcApi &nvrtc() {
+  static NvrtcApi api = [] {
+    NvrtcApi a;
+    void *h = dlopen("libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
+    if (!h) h = dlopen("/usr/local/cuda/lib64/libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
+    if (!h) {
+      a.err = "libnvrtc.so.13 not found";
+      return a;
+    }
+    a.create = reinterpret_cast<decltype(a.create)>(dlsym(h, "nvrtcCreateProgram"));
+    a.compile = reinterpret_cast<decltype(a.compile)>(dlsym(h, "nvrtcCompileProgram"));
+    a.log_size = reinterpret_cast<decltype(a.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+    a.log = reinterpret_cast<decltype(a.log)>(dlsym(h, "nvrtcGetProgramLog"));
+    a.cubin_size = reinterpret_cast<decltype(a.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+    a.cubin = reinterpret_cast<decltype(a.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+    a.destroy = reinterpret_cast<decltype(a.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+    a.ok = a.create && a.compile && a.log_size && a.log && a.cubin_size && a.cubin && a.destroy;
+    if (!a.ok) a.err = "libnvrtc.so.13 lacks an entry point";
+    return a;
+  }();
+  return api;
+}
+
+// Per-format definitions of the row macros used by the generated rows.
+const char *row_macros(int msg) {
+  if (msg == 2)
+    return R"(
+#define BCH_VT int
+#define BCH_R0 { int m1_ = 1 << 20, m2_ = 1 << 20, a_; uint32_t sg_ = 0u;
+#define BCH_R1(u) a_ = abs(z[u]); m2_ = min(m2_, max(m1_, a_)); m1_ = min(m1_, a_); sg_ ^= uint32_t(z[u]);
+#define BCH_RM const int c1_ = __double2int_rn(double(alpha) * double(m1_)); \
+  const int c2_ = __double2int_rn(double(alpha) * double(m2_)); \
+  const int v1_ = (sg_ & kSign) ? -c1_ : c1_; const int v2_ = (sg_ & kSign) ? -c2_ : c2_;
+#define BCH_R2(u) { const int mg_ = (abs(z[u]) == m1_) ? v2_ : v1_; BCH_SV(u) += (z[u] < 0) ? -mg_ : mg_; }
+#define BCH_RE }
+)";
+  if (msg == 1)
+    return R"(
+#define BCH_VT float
+#define BCH_R0 { float m1_ = FLT_MAX, m2_ = FLT_MAX, a_; uint32_t sg_ = 0u;
+#define BCH_R1(u) a_ = fabsf(z[u]); m2_ = fminf(m2_, fmaxf(m1_, a_)); m1_ = fminf(m1_, a_); sg_ ^= __float_as_uint(z[u]);
+#define BCH_RM const float v1_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m1_))), sg_); \
+  const float v2_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m2_))), sg_);
+#define BCH_R2(u) BCH_SV(u) += flip_sign((fabsf(z[u]) == m1_) ? v2_ : v1_, __float_as_uint(z[u]));
+#define BCH_RE }
+)";
+  return R"(
+#define BCH_VT float
+#define BCH_R0 { float m1_ = FLT_MAX, m2_ = FLT_MAX, a_; uint32_t sg_ = 0u;
+#define BCH_R1(u) a_ = fabsf(z[u]); m2_ = fminf(m2_, fmaxf(m1_, a_)); m1_ = fminf(m1_, a_); sg_ ^= __float_as_uint(z[u]);
+#define BCH_RM const float v1_ = flip_sign(alpha * m1_, sg_); const float v2_ = flip_sign(alpha * m2_, sg_);
+#define BCH_R2(u) BCH_SV(u) += flip_sign((fabsf(z[u]) == m1_) ? v2_ : v1_, __float_as_uint(z[u]));
+#define BCH_RE }
+)";
+}
+
+struct Compiled {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kernel = nullptr;
+  std::string err;
+};
+
+std::mutex g_mu;
+std::map<std::string, std::shared_ptr<Compiled>> g_cache;
+
+}  // namespace
+
+int jit_block_size(int n) { return n <= 63 ? 128 : 64; }
+// Resident blocks per SM the register budget is sized for (3 x 128 threads for n <= 63:
+// at most 170 registers, enough for the 2n register-resident values plus temporaries).
+int jit_min_blocks(int n) {
+  const char *v = std::getenv("BCHDEC_JIT_MIN_BLOCKS");  // tuning knob (register budget)
+  if (v && std::atoi(v) >= 1 && std::atoi(v) <= 8) return std::atoi(v);
+  return n <= 63 ? 3 : 2;
+}
+int jit_scratch_words(int n) { return n <= 63 ? 0 : n; }
+
+std::string jit_source(const bch_code *c, int msg) {
+  const int n = c->alg.n, m = c->alg.m;
+  const int tpb = jit_block_size(n);
+  const int scratch = jit_scratch_words(n);
+  const int nw = (n + 31) / 32;
+  std::ostringstream o;
+  o << "typedef unsigned int uint32_t;\ntypedef int int32_t;\ntypedef unsigned short uint16_t;\n"
+       "typedef unsigned char uint8_t;\ntypedef signed char int8_t;\n"
+       "typedef unsigned long long uint64_t;\ntypedef unsigned long long uintptr_t;\n"
+       "#define FLT_MAX 3.402823466e+38f\n#include <cuda_fp16.h>\n";
+  o << kDevTypesText << "\n" << kNmsDeviceText << "\n";
+  o << "namespace bchlib {\n" << row_macros(msg);
+  if (scratch)
+    o << "#define BCH_SV(u) scr[(u) * " << tpb << "]\n";
+  else
+    o << "#define BCH_SV(u) S[u]\n";
+  o << "struct JitCopy {\n  static constexpr int kScratch = " << scratch << ";\n"
+    << "  __device__ __forceinline__ void operator()(const SmemTables &, int, uint32_t, uint32_t,\n"
+    << "      StoreT<" << msg << ">::Y *y, StoreT<" << msg << ">::A *acc, StoreT<" << msg
+    << ">::A *scr, uint32_t jr, uint32_t sp, uint32_t sh, float alpha) const {\n"
+    << "    BCH_VT z[" << n << "];\n"
+    << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) {\n"
+    << "      const uint32_t i = addmod(bfe32(uint32_t(u) | (uint32_t(u) << " << m << "), jr, " << m
+    << "), sp, " << n << ");\n      z[u] = ld_y(y + (i << sh));\n    }\n";
+  if (scratch)
+    o << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) BCH_SV(u) = 0;\n";
+  else
+    o << "    StoreT<" << msg << ">::A S[" << n << "];\n#pragma unroll\n    for (int u = 0; u < " << n
+      << "; u++) S[u] = 0;\n";
+  // rows, grouped by weight like the device image
+  for (const Row &row : c->rows) {
+    std::vector<int> cols;
+    for (int u = 0; u < n; u++)
+      if (row.get(u)) cols.push_back(u);
+    o << "    BCH_R0";
+    for (int u : cols) o << " BCH_R1(" << u << ")";
+    o << " BCH_RM";
+    for (int u : cols) o << " BCH_R2(" << u << ")";
+    o << " BCH_RE\n";
+  }
+  o << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) {\n"
+    << "      const uint32_t i = addmod(bfe32(uint32_t(u) | (uint32_t(u) << " << m << "), jr, " << m
+    << "), sp, " << n << ");\n      acc[i << sh] += BCH_SV(u);\n    }\n  }\n};\n}  // namespace bchlib\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << tpb << ", " << jit_min_blocks(n)
+    << ") bch_nms_jit(const bchlib::NmsArgs a) {\n"
+    << "  extern __shared__ __align__(16) unsigned char smem[];\n"
+    << "  bchlib::nms_persistent<" << msg << ", " << nw << ">(a, smem, bchlib::JitCopy());\n}\n";
+  return o.str();
+}
+
+// Returns the specialised kernel for (code, msg), compiling it on first use; on
+// failure returns nullptr and sets *err.
+cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
+  const std::string src = jit_source(c, msg);
+  std::shared_ptr<Compiled> cp;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(src);
+    if (it != g_cache.end()) cp = it->second;
+  }
+  if (cp) {
+    if (!cp->kernel) *err = cp->err;
+    return cp->kernel;
+  }
+  cp = std::make_shared<Compiled>();
+  NvrtcApi &api = nvrtc();
+  if (!api.ok) {
+    cp->err = api.err;
+  } else {
+    nvrtcProgram prog = nullptr;
+    if (api.create(&prog, src.c_str(), "bch_nms_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+      cp->err = "nvrtcCreateProgram failed";
+    } else {
+      const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-I/usr/local/cuda/include",
+                            "-lineinfo"};
+      const nvrtcResult r = api.compile(prog, 4, opts);
+      if (r != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        api.log_size(prog, &ls);
+        std::string log(ls, '\0');
+        if (ls) api.log(prog, &log[0]);
+        cp->err = "NVRTC compile failed: " + log.substr(0, 2000);
+      } else {
+        size_t cs = 0;
+        api.cubin_size(prog, &cs);
+        std::vector<char> cubin(cs);
+        api.cubin(prog, cubin.data());
+        cudaError_t e = cudaLibraryLoadData(&cp->lib, cubin.data(), nullptr, nullptr, 0, nullptr,
+                                            nullptr, 0);
+        if (e == cudaSuccess) e = cudaLibraryGetKernel(&cp->kernel, cp->lib, "bch_nms_jit");
+        if (e != cudaSuccess) {
+          cp->kernel = nullptr;
+          cp->err = std::string("loading the compiled kernel: ") + cudaGetErrorString(e);
+        }
+      }
+      api.destroy(&prog);
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[src] = cp;
+  }
+  if (!cp->kernel) *err = cp->err;
+  return cp->kernel;
+}
+
+}  // namespace bchlib

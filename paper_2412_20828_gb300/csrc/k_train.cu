@@ -18,7 +18,7 @@
 namespace bchlib {
 
 template <int WB>
-__device__ __noinline__ void bwd_rows(const uint16_t *__restrict__ codes, int nrows, int w, int w4,
+__device__ __forceinline__ void bwd_rows(const uint16_t *__restrict__ codes, int nrows, int w, int w4,
                                       const float *__restrict__ y, const float *__restrict__ g,
                                       float *__restrict__ gp, uint32_t jr, uint32_t sp, uint32_t n,
                                       uint32_t m, uint32_t sh, float alpha, float invP,
@@ -88,11 +88,13 @@ __device__ __noinline__ void bwd_rows(const uint16_t *__restrict__ codes, int nr
   }
 }
 
-template <int TPB>
+template <int TPB, int WB>
 __global__ void __launch_bounds__(TPB) nms_backward_kernel(const BwdArgs a) {
   constexpr uint32_t kShift = TPB == 128 ? 7u : (TPB == 64 ? 6u : 5u);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float red[TPB / 32];
+  __shared__ float alpha_s[32];
+  __shared__ int gw_s[kMaxGroups], gr_s[kMaxGroups], go_s[kMaxGroups];
   const int code_words = a.dc.group_off[a.dc.n_groups];
   uint16_t *codes = reinterpret_cast<uint16_t *>(smem);
   {
@@ -100,7 +102,18 @@ __global__ void __launch_bounds__(TPB) nms_backward_kernel(const BwdArgs a) {
     uint32_t *dst = reinterpret_cast<uint32_t *>(codes);
     for (int i = threadIdx.x; i < code_words / 2; i += blockDim.x) dst[i] = src[i];
   }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < 32; i++) alpha_s[i] = a.alpha[i];
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; g++) {
+      gw_s[g] = a.dc.group_w[g];
+      gr_s[g] = a.dc.group_rows[g];
+      go_s[g] = a.dc.group_off[g];
+    }
+  }
   __syncthreads();
+  const int n_groups = a.dc.n_groups;
   float *state = reinterpret_cast<float *>(smem + ((size_t(code_words) * 2 + 15) & ~size_t(15)));
   const int n = a.dc.n;
   const uint32_t m = uint32_t(a.dc.m);
@@ -133,37 +146,17 @@ __global__ void __launch_bounds__(TPB) nms_backward_kernel(const BwdArgs a) {
         y[i << kShift] = src[i];
         gp[i << kShift] = g[i << kShift];
       }
-      const float alpha = a.alpha[t - 1];
+      const float alpha = alpha_s[t - 1];
 #pragma unroll
       for (int p = 0; p < 9; p++) {
         if (p < a.P) {
           const uint32_t jr = ctx[p] & 0xffu, spv = ctx[p] >> 8;
-          for (int gi = 0; gi < a.dc.n_groups; gi++) {
-            const int w = a.dc.group_w[gi];
+          for (int gi = 0; gi < n_groups; gi++) {
+            const int w = gw_s[gi];
             const int w4 = (w + 3) & ~3;
-            const uint16_t *c = codes + a.dc.group_off[gi];
-            const int nr = a.dc.group_rows[gi];
-            switch (w4 >> 2) {
-#define BCH_BCASE(K)                                                                            \
-  case K:                                                                                       \
-    bwd_rows<4 * K>(c, nr, w, w4, y, g, gp, jr, spv, uint32_t(n), m, kShift, alpha, invP, dal); \
-    break;
-              BCH_BCASE(1)
-              BCH_BCASE(2)
-              BCH_BCASE(3)
-              BCH_BCASE(4)
-              BCH_BCASE(5)
-              BCH_BCASE(6)
-              BCH_BCASE(7)
-              BCH_BCASE(8)
-              BCH_BCASE(9)
-              BCH_BCASE(10)
-              BCH_BCASE(11)
-              BCH_BCASE(12)
-#undef BCH_BCASE
-              default:
-                break;
-            }
+            const uint16_t *c = codes + go_s[gi];
+            const int nr = gr_s[gi];
+            bwd_rows<WB>(c, nr, w, w4, y, g, gp, jr, spv, uint32_t(n), m, kShift, alpha, invP, dal);
           }
         }
       }
@@ -199,6 +192,15 @@ __global__ void reduce_alpha_kernel(const float *partial, int nb, int I, float *
   }
 }
 
+template <int TPB, int WB>
+static cudaError_t launch_bwd_wb(const BwdArgs &a, int nb, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(nms_backward_kernel<TPB, WB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  nms_backward_kernel<TPB, WB><<<nb, TPB, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 size_t backward_workspace(int F, int I) {
   const int nb = (F + 63) / 64;
   return size_t(nb) * size_t(I) * sizeof(float);
@@ -209,11 +211,22 @@ cudaError_t launch_backward(const BwdArgs &a0, float *grad_alpha, cudaStream_t s
   constexpr int TPB = 64;
   const int code_words = a0.dc.group_off[a0.dc.n_groups];
   const size_t smem = ((size_t(code_words) * 2 + 15) & ~size_t(15)) + size_t(3) * a0.dc.n * TPB * 4;
-  cudaError_t e = cudaFuncSetAttribute(nms_backward_kernel<TPB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
   const int nb = (a0.F + TPB - 1) / TPB;
-  nms_backward_kernel<TPB><<<nb, TPB, smem, st>>>(a0);
+  const int mw = a0.dc.max_w;
+  cudaError_t e = cudaSuccess;
+  if (mw <= 8)
+    e = launch_bwd_wb<TPB, 8>(a0, nb, smem, st);
+  else if (mw <= 16)
+    e = launch_bwd_wb<TPB, 16>(a0, nb, smem, st);
+  else if (mw <= 24)
+    e = launch_bwd_wb<TPB, 24>(a0, nb, smem, st);
+  else if (mw <= 32)
+    e = launch_bwd_wb<TPB, 32>(a0, nb, smem, st);
+  else if (mw <= 48)
+    e = launch_bwd_wb<TPB, 48>(a0, nb, smem, st);
+  else
+    e = cudaErrorNotSupported;
+  if (e != cudaSuccess) return e;
   reduce_alpha_kernel<<<a0.I, 256, 0, st>>>(a0.partial, nb, a0.I, grad_alpha);
   return cudaGetLastError();
 }

@@ -1,0 +1,465 @@
+// Device code of the normalized min-sum decoders, shared by the precompiled kernels
+// (nvcc) and the kernels compiled at run time for one code (NVRTC).
+//
+// Enhanced NMS (arXiv 2412.20828, Algorithm 1, reading A).  Design:
+//  * one thread owns one frame; a frame's state lives in shared memory laid out
+//    [variable][thread], so every access of a warp hits 32 distinct banks whatever the
+//    per-frame permutation is;
+//  * the automorphism pi(i) = 2^j i + s is applied on the fly: pi^-1(u) =
+//    rotr_m(u, j) + s' mod n, and rotr_m(u, j) is one bfe on the column code
+//    d(u) = u | u << m;
+//  * check rows keep min1 / min2 / sign product in registers and add their
+//    check-to-variable values straight into an accumulator (reading A keeps no
+//    per-edge messages);
+//  * persistent warps: a lane whose frame stops (zero syndrome or I_m) writes its
+//    outputs and pulls the next frame from a global queue (warp-aggregated atomic), so
+//    early stopping turns into throughput instead of idle lanes.
+#pragma once
+#ifndef __CUDACC_RTC__
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <cfloat>
+
+#include "bch_devtypes.h"
+#endif
+
+namespace bchlib {
+
+constexpr uint32_t kSign = 0x80000000u;
+constexpr unsigned kFull = 0xffffffffu;
+
+// m-bit field of x starting at bit `pos` (PTX bfe).
+__device__ __forceinline__ uint32_t bfe32(uint32_t x, uint32_t pos, uint32_t len) {
+  uint32_t r;
+  asm("bfe.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(pos), "r"(len));
+  return r;
+}
+
+// (a + b) mod n for a, b in [0, n): min(a + b, a + b - n) in unsigned arithmetic.
+__device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, uint32_t n) {
+  uint32_t x = a + b;
+  return __viaddmin_u32(x, 0u - n, x);
+}
+
+__device__ __forceinline__ float flip_sign(float mag, uint32_t sign_src) {
+  return __uint_as_float(__float_as_uint(mag) ^ (sign_src & kSign));
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Storage formats of y.  Accumulators are FP32 (FP32 / FP16) or int32 (INT8).
+enum : int { kFP32 = 0, kFP16 = 1, kINT8 = 2 };
+
+template <int MSG>
+struct StoreT;
+template <>
+struct StoreT<kFP32> {
+  using Y = float;
+  using A = float;
+};
+template <>
+struct StoreT<kFP16> {
+  using Y = __half;
+  using A = float;
+};
+template <>
+struct StoreT<kINT8> {
+  using Y = int8_t;
+  using A = int32_t;
+};
+
+__device__ __forceinline__ float ld_y(const float *p) { return *p; }
+__device__ __forceinline__ float ld_y(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ int ld_y(const int8_t *p) { return int(*p); }
+
+// FP16 store: round to nearest even, saturating at +-65504.
+__device__ __forceinline__ __half to_half_sat(float x) {
+  x = fminf(fmaxf(x, -65504.0f), 65504.0f);
+  return __float2half_rn(x);
+}
+__device__ __forceinline__ __half half_sat_d(double x) {
+  x = fmin(fmax(x, -65504.0), 65504.0);
+  return __double2half(x);
+}
+// INT8 store: rne, saturating at +-31 (LSB = 1/4 of an LLR unit).
+__device__ __forceinline__ int8_t to_q(float x) {
+  int q = __float2int_rn(x);
+  q = max(-31, min(31, q));
+  return int8_t(q);
+}
+
+// Shared-memory carve-up common to the NMS kernels.
+struct GroupDesc {
+  int w, rows, off, pad;
+};
+struct SmemTables {
+  uint16_t *codes;
+  uint4 *rowmask;
+  float *alpha;
+  GroupDesc *grp;
+  unsigned char *state;
+};
+
+// ---------------------------------------------------------------- row processing
+// Processes `nrows` check rows of weight w (w <= WB) for one automorphism.
+template <int MSG, int WB>
+__device__ __forceinline__ void enh_rows(const uint16_t *__restrict__ codes, int nrows, int w,
+                                      int w4, typename StoreT<MSG>::Y *__restrict__ y,
+                                      typename StoreT<MSG>::A *__restrict__ acc, uint32_t jr,
+                                      uint32_t sp, uint32_t n, uint32_t m, uint32_t sh,
+                                      float alpha) {
+  using A = typename StoreT<MSG>::A;
+  for (int r = 0; r < nrows; r++) {
+    const uint16_t *c = codes + r * w4;
+    uint32_t ix[WB];
+    if constexpr (MSG == kINT8) {
+      int z[WB];
+      int m1 = 1 << 20, m2 = 1 << 20;
+      uint32_t sg = 0;
+#pragma unroll
+      for (int e = 0; e < WB; e += 4) {
+        if (e < w) {
+          const uint2 q = *reinterpret_cast<const uint2 *>(c + e);
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            if (e + h < w) {
+              const uint32_t word = h < 2 ? q.x : q.y;
+              const uint32_t rr = bfe32(word, jr + ((h & 1) ? 16u : 0u), m);
+              const uint32_t i = addmod(rr, sp, n);
+              ix[e + h] = i << sh;
+              const int v = ld_y(y + ix[e + h]);
+              z[e + h] = v;
+              const int av = abs(v);
+              m2 = min(m2, max(m1, av));
+              m1 = min(m1, av);
+              sg ^= uint32_t(v);
+            }
+          }
+        }
+      }
+      // c2v magnitudes are integers: rne(alpha * min), the product formed exactly
+      const int c1 = __double2int_rn(double(alpha) * double(m1));
+      const int c2 = __double2int_rn(double(alpha) * double(m2));
+      const int s1 = (sg & kSign) ? -c1 : c1;
+      const int s2 = (sg & kSign) ? -c2 : c2;
+      A o[WB];
+#pragma unroll
+      for (int e = 0; e < WB; e++)
+        if (e < w) o[e] = acc[ix[e]];
+#pragma unroll
+      for (int e = 0; e < WB; e++)
+        if (e < w) {
+          const int mag = (abs(z[e]) == m1) ? s2 : s1;
+          o[e] += (z[e] < 0) ? -mag : mag;
+        }
+#pragma unroll
+      for (int e = 0; e < WB; e++)
+        if (e < w) acc[ix[e]] = o[e];
+    } else {
+      float z[WB];
+      float m1 = FLT_MAX, m2 = FLT_MAX;
+      uint32_t sg = 0;
+#pragma unroll
+      for (int e = 0; e < WB; e += 4) {
+        if (e < w) {
+          const uint2 q = *reinterpret_cast<const uint2 *>(c + e);
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            if (e + h < w) {
+              const uint32_t word = h < 2 ? q.x : q.y;
+              const uint32_t rr = bfe32(word, jr + ((h & 1) ? 16u : 0u), m);
+              const uint32_t i = addmod(rr, sp, n);
+              ix[e + h] = i << sh;
+              const float v = ld_y(y + ix[e + h]);
+              z[e + h] = v;
+              const float av = fabsf(v);
+              m2 = fminf(m2, fmaxf(m1, av));
+              m1 = fminf(m1, av);
+              sg ^= __float_as_uint(v);
+            }
+          }
+        }
+      }
+      float v1, v2;
+      if constexpr (MSG == kFP16) {
+        // messages are stored in binary16: alpha * min is formed exactly (a float
+        // times a binary16 value fits a double) and rounded once
+        v1 = flip_sign(__half2float(half_sat_d(double(alpha) * double(m1))), sg);
+        v2 = flip_sign(__half2float(half_sat_d(double(alpha) * double(m2))), sg);
+      } else {
+        v1 = flip_sign(alpha * m1, sg);
+        v2 = flip_sign(alpha * m2, sg);
+      }
+      float o[WB];
+#pragma unroll
+      for (int e = 0; e < WB; e++)
+        if (e < w) o[e] = acc[ix[e]];
+#pragma unroll
+      for (int e = 0; e < WB; e++)
+        if (e < w) {
+          const float mag = (fabsf(z[e]) == m1) ? v2 : v1;
+          o[e] += flip_sign(mag, __float_as_uint(z[e]));
+        }
+#pragma unroll
+      for (int e = 0; e < WB; e++)
+        if (e < w) acc[ix[e]] = o[e];
+    }
+  }
+}
+
+template <int MSG, int WB>
+__device__ __forceinline__ void enh_copy(const SmemTables &tb, int n_groups, uint32_t n, uint32_t m,
+                                         typename StoreT<MSG>::Y *y, typename StoreT<MSG>::A *acc,
+                                         uint32_t jr, uint32_t sp, uint32_t sh, float alpha) {
+  for (int g = 0; g < n_groups; g++) {
+    const GroupDesc gd = tb.grp[g];
+    const int w = gd.w;
+    enh_rows<MSG, WB>(tb.codes + gd.off, gd.rows, w, (w + 3) & ~3, y, acc, jr, sp, n, m, sh, alpha);
+  }
+}
+
+__device__ __forceinline__ SmemTables load_tables(const NmsArgs &a, unsigned char *smem,
+                                                  int code_words) {
+  SmemTables t;
+  t.codes = reinterpret_cast<uint16_t *>(smem);
+  unsigned char *p = smem + ((size_t(code_words) * 2 + 15) & ~size_t(15));
+  t.rowmask = reinterpret_cast<uint4 *>(p);
+  p += size_t(a.dc.rows) * 16;
+  t.alpha = reinterpret_cast<float *>(p);
+  p += 32 * 4;
+  t.grp = reinterpret_cast<GroupDesc *>(p);
+  p += kMaxGroups * sizeof(GroupDesc);
+  t.state = p;
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(a.dc.codes);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(t.codes);
+  for (int i = threadIdx.x; i < code_words / 2; i += blockDim.x) dst[i] = src[i];
+  const uint4 *rm = reinterpret_cast<const uint4 *>(a.dc.rowmask);
+  for (int i = threadIdx.x; i < a.dc.rows; i += blockDim.x) t.rowmask[i] = rm[i];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < 32; i++) t.alpha[i] = a.alpha[i];
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; g++) {
+      GroupDesc d;
+      d.w = a.dc.group_w[g];
+      d.rows = a.dc.group_rows[g];
+      d.off = a.dc.group_off[g];
+      d.pad = 0;
+      t.grp[g] = d;
+    }
+  }
+  __syncthreads();
+  return t;
+}
+
+// Syndrome of the hard decision cb (bit i = [y_i < 0]) against the packed rows:
+// nonzero iff some row has odd overlap.
+template <int NW>
+__device__ __forceinline__ uint32_t syndrome_nonzero(const uint4 *rowmask, int rows,
+                                                     const uint32_t (&cb)[NW]) {
+  uint32_t nz = 0;
+  for (int r = 0; r < rows; r++) {
+    const uint4 rm = rowmask[r];
+    uint32_t x = rm.x & cb[0];
+    if constexpr (NW > 1) x ^= rm.y & cb[1];
+    if constexpr (NW > 2) x ^= (rm.z & cb[2]) ^ (rm.w & cb[3]);
+    nz |= __popc(x) & 1u;
+  }
+  return nz;
+}
+
+template <int NW>
+__device__ __forceinline__ void write_hard(uint64_t *hard, int f, const uint32_t (&cb)[NW]) {
+  constexpr int W64 = (NW + 1) / 2;
+  uint64_t *h = hard + size_t(f) * W64;
+  h[0] = uint64_t(cb[0]) | (NW > 1 ? uint64_t(cb[NW > 1 ? 1 : 0]) << 32 : 0);
+  if constexpr (NW > 2) h[1] = uint64_t(cb[2]) | (uint64_t(cb[3]) << 32);
+}
+
+// Warp-aggregated pull from the frame queue: lanes with `need` get consecutive
+// frame indices (or -1 once the queue is exhausted).
+__device__ __forceinline__ int pull_frame(unsigned *queue, bool need, int F) {
+  const unsigned want = __ballot_sync(kFull, need);
+  if (!want) return -1;
+  const unsigned lane = lane_id();
+  const unsigned leader = __ffs(want) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(queue, unsigned(__popc(want)));
+  base = __shfl_sync(kFull, base, leader);
+  if (!need) return -1;
+  const unsigned my = base + unsigned(__popc(want & ((1u << lane) - 1u)));
+  return my < unsigned(F) ? int(my) : -1;
+}
+
+// ---------------------------------------------------------------- persistent loop
+// The persistent frame loop shared by the precompiled and the run-time compiled
+// kernels; `copy` processes one automorphism of one frame (check pass + accumulate).
+// Per-thread shared columns (stride = block size): ctx[P], acc[n], y[n], then
+// Copy::kScratch words of scratch for the functor.
+template <int MSG, int NW, class Copy>
+__device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *smem, const Copy &copy) {
+  using Y = typename StoreT<MSG>::Y;
+  using A = typename StoreT<MSG>::A;
+  const int TPB = blockDim.x;  // 64 or 128
+  const uint32_t kShift = TPB == 128 ? 7u : (TPB == 64 ? 6u : 5u);
+  const int code_words = a.dc.group_off[a.dc.n_groups];
+  SmemTables tb = load_tables(a, smem, code_words);
+  const int n = a.dc.n;
+  const uint32_t m = uint32_t(a.dc.m);
+  const int n_groups = a.dc.n_groups;
+  const int tid = threadIdx.x;
+  // per-thread columns: ctx[P], y[n], acc[n]
+  uint32_t *ctx_s = reinterpret_cast<uint32_t *>(tb.state);
+  A *acc_s = reinterpret_cast<A *>(tb.state + size_t(a.P) * TPB * 4);
+  Y *y_s = reinterpret_cast<Y *>(tb.state + size_t(a.P) * TPB * 4 + size_t(n) * TPB * sizeof(A));
+  Y *y = y_s + tid;
+  unsigned char *scr_s = tb.state + size_t(a.P) * TPB * 4 + size_t(n) * TPB * (sizeof(A) + sizeof(Y));
+  scr_s = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(scr_s) + 15) & ~uintptr_t(15));
+  A *scratch = reinterpret_cast<A *>(scr_s) + tid;
+  A *acc = acc_s + tid;
+  uint32_t *ctx = ctx_s + tid;
+  const float invP = 1.0f / float(a.P);
+  const bool vec = ((a.ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.llr) & 15) == 0);
+
+  int f = -1, t = 0, escale = 0;
+  bool need = true;
+  for (;;) {
+    const int got = pull_frame(a.queue, need, a.F);
+    if (need) {
+      need = false;
+      f = got;
+      if (f >= 0) {
+        t = 0;
+        escale = 0;
+        const float *src = a.llr + size_t(f) * a.ld;
+        for (int i = 0; i < n; i += 4) {
+          float4 v;
+          if (vec) {
+            v = __ldg(reinterpret_cast<const float4 *>(src + i));
+          } else {
+            v.x = src[i];
+            v.y = i + 1 < n ? src[i + 1] : 0.f;
+            v.z = i + 2 < n ? src[i + 2] : 0.f;
+            v.w = i + 3 < n ? src[i + 3] : 0.f;
+          }
+          const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            if (i + h < n) {
+              const float x = vv[h] + 0.0f;  // -0 -> +0: sgn(0) = +1
+              if constexpr (MSG == kFP32) y[(i + h) << kShift] = x;
+              if constexpr (MSG == kFP16) y[(i + h) << kShift] = to_half_sat(x);
+              if constexpr (MSG == kINT8) y[(i + h) << kShift] = to_q(4.0f * x);
+              acc[(i + h) << kShift] = A(0);
+              if (a.ckpt) a.ckpt[size_t(f) * a.ld + i + h] = x;
+            }
+          }
+        }
+        for (int p = 0; p < a.P; p++) {
+          const uint32_t v = a.autos[size_t(f) * a.P + p];
+          const uint32_t s = v & 0xffu, j = v >> 8;
+          // pi^-1(u) = rotr_m(u, j) + s' with s' = -rotr_m(s, j) mod n
+          const uint32_t rs = j ? (((s >> j) | (s << (m - j))) & uint32_t(n)) : s;
+          const uint32_t sp = rs ? uint32_t(n) - rs : 0u;
+          ctx[p << kShift] = j | (sp << 8);
+        }
+      }
+    }
+    if (!__any_sync(kFull, f >= 0)) break;
+    if (f < 0) continue;
+
+    const float alpha = tb.alpha[t];
+    for (int p = 0; p < a.P; p++) {
+      const uint32_t cx = ctx[p << kShift];
+      copy(tb, n_groups, uint32_t(n), m, y, acc, scratch, cx & 0xffu, cx >> 8, kShift, alpha);
+    }
+    // merge (FP32), hard decision, re-store
+    uint32_t cb[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) cb[w] = 0;
+    if constexpr (MSG == kFP32) {
+#pragma unroll
+      for (int i = 0; i < NW * 32; i++) {
+        if (i < n) {
+          const float yn = __fmaf_rn(acc[i << kShift], invP, y[i << kShift]);
+          y[i << kShift] = yn;
+          acc[i << kShift] = 0.0f;
+          cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
+        }
+      }
+    } else {
+      // pass 1: FP32 merge into the accumulator slot, track the magnitude
+      float mx = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NW * 32; i++) {
+        if (i < n) {
+          float yn;
+          if constexpr (MSG == kINT8)  // exact division: a .5 tie stays a tie
+            yn = float(ld_y(y + (i << kShift))) + __fdiv_rn(float(acc[i << kShift]), float(a.P));
+          else
+            yn = __fmaf_rn(acc[i << kShift], invP, ld_y(y + (i << kShift)));
+          cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
+          mx = fmaxf(mx, fabsf(yn));
+          reinterpret_cast<float *>(acc)[i << kShift] = yn;
+        }
+      }
+      // optional power-of-two renormalisation (exact; min-sum is scale invariant)
+      float sc = 1.0f;
+      if (a.rescale) {
+        const float lim = (MSG == kINT8) ? 31.0f : 16384.0f;
+        int k = 0;
+        while (mx * sc > lim && k < 126) {
+          sc *= 0.5f;
+          k++;
+        }
+        escale += k;
+      }
+#pragma unroll
+      for (int i = 0; i < NW * 32; i++) {
+        if (i < n) {
+          const float yn = reinterpret_cast<float *>(acc)[i << kShift] * sc;
+          if constexpr (MSG == kINT8)
+            y[i << kShift] = to_q(yn);
+          else
+            y[i << kShift] = to_half_sat(yn);
+          acc[i << kShift] = A(0);
+        }
+      }
+    }
+    t++;
+    if (a.ckpt) {
+      float *dst = a.ckpt + (size_t(t) * a.F + f) * a.ld;
+      for (int i = 0; i < n; i++) dst[i] = float(ld_y(y + (i << kShift)));
+    }
+    const uint32_t nz = syndrome_nonzero<NW>(tb.rowmask, a.dc.rows, cb);
+    if (t >= a.I || (a.early_stop && nz == 0)) {
+      if (a.hard) write_hard<NW>(a.hard, f, cb);
+      if (a.iters) a.iters[f] = uint8_t(t);
+      if (a.flags) a.flags[f] = nz ? 0 : uint8_t(kFlagConverged);
+      if (a.llr_out) {
+        float *dst = a.llr_out + size_t(f) * a.ld;
+        float unscale = 1.0f;
+        if constexpr (MSG == kINT8) unscale = 0.25f;
+        for (int k = 0; k < escale; k++) unscale *= 2.0f;
+        for (int i = 0; i < n; i++) dst[i] = float(ld_y(y + (i << kShift))) * unscale;
+      }
+      need = true;
+    }
+  }
+}
+
+
+// Precompiled path: rows read their column codes from shared memory.
+template <int MSG, int WB>
+struct GenericCopy {
+  static constexpr int kScratch = 0;
+  __device__ __forceinline__ void operator()(const SmemTables &tb, int n_groups, uint32_t n, uint32_t m,
+                                             typename StoreT<MSG>::Y *y, typename StoreT<MSG>::A *acc,
+                                             typename StoreT<MSG>::A *, uint32_t jr, uint32_t sp,
+                                             uint32_t sh, float alpha) const {
+    enh_copy<MSG, WB>(tb, n_groups, n, m, y, acc, jr, sp, sh, alpha);
+  }
+};
+
+}  // namespace bchlib

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import ambiguous_frames, autos_dev, frames, rel_close, to_dev
+from helpers import ambiguous_frames, autos_dev, frame_envelope, frames, rel_close, to_dev
 from paper_2412_20828_gb300 import bchdec as B
 
 pytestmark = pytest.mark.gpu
@@ -111,15 +111,15 @@ def test_enhanced_full_decode(torch_cuda, nk, ebn0):
     g = run_nms(torch_cuda, c, llr, autos, 12, alpha)
     ref = O.nms_enhanced(c.dense(), llr, autos, 12, alpha, trace=True, threads=None)
     amb = ambiguous_frames(llr, ref, n)
-    assert amb.mean() < 0.05
+    assert amb.mean() < 0.1
     ok = ~amb
     assert np.array_equal(g["iters"][ok], ref["iters"][ok])
     assert np.array_equal(g["hard"][ok], ref["hard"][ok])
     assert np.array_equal(g["flags"][ok] & 1, ref["converged"][ok])
-    last = np.maximum(ref["iters"] - 1, 0)
-    mag = ref["mag"][np.arange(F), last]
-    close = rel_close(g["y"][:, :n], ref["y"], mag)
-    assert close[ok].all()
+    env = frame_envelope(ref)[:, None]
+    err = np.abs(g["y"][:, :n] - ref["y"]) / (1e-5 * np.maximum(np.abs(ref["y"]), env))
+    assert err[ok].max() <= 1.0, f"worst error {err[ok].max():.3g} x tolerance"
+
 
 
 def test_enhanced_nine_automorphisms_and_unaligned_ld(torch_cuda):
@@ -191,13 +191,18 @@ def test_plain_nms_standard_h(torch_cuda, ebn0):
     cw, llr = frames(n, k, F, ebn0, 500, ld=64)
     g = run_nms(torch_cuda, c, llr, None, 8, 0.78, n_autos=0)
     ref = O.nms_plain(c.dense(), llr, 8, 0.78, threads=None)
-    amb = np.any(np.abs(llr[:, :n]) < 1e-3, axis=1) | (np.abs(ref["y"]) < 1e-3).any(1)
+    amb = np.any(np.abs(llr[:, :n]) < 1e-3, axis=1) | (ref["margin_rel"] < 1e-4)
+    assert amb.mean() < 0.1
     ok = ~amb
     assert np.array_equal(g["iters"][ok], ref["iters"][ok])
-    agree = np.all(g["hard"] == ref["hard"], axis=1)
-    assert agree[ok].mean() > 0.995
-    close = rel_close(g["y"][:, :n], ref["y"], np.abs(ref["y"]) + np.abs(llr[:, :n]) * 0 + 1.0)
-    assert close[ok & agree].mean() > 0.99
+    assert np.array_equal(g["hard"][ok], ref["hard"][ok])
+    env = ref["env"][:, None]
+    err = np.abs(g["y"][:, :n] - ref["y"]) / (1e-5 * np.maximum(np.abs(ref["y"]), env))
+    assert err[ok].max() <= 1.0, f"worst error {err[ok].max():.3g} x tolerance"
+    # one iteration from the same input: element-wise against the operand magnitude
+    g1 = run_nms(torch_cuda, c, llr, None, 1, 0.78, n_autos=0, early_stop=False)
+    r1 = O.nms_plain(c.dense(), llr, 1, 0.78, early_stop=False)
+    assert rel_close(g1["y"][:, :n], r1["y"], r1["env"][:, None]).all()
 
 
 # ------------------------------------------------------------------ OSD and hybrid
@@ -291,3 +296,29 @@ def test_count_errors(torch_cuda):
     assert got[0] == F and got[1] == fe.sum() and got[2] == flip.sum()
     assert got[3] == (fe & ((fl & 1) == 1) & ((fl & 2) == 0)).sum()
     assert got[4] == ((fl & 2) > 0).sum() and got[5] == it.sum() and got[6] == (fl & 1).sum()
+
+
+# ------------------------------------------------------------------ kernel variants
+@pytest.mark.parametrize("msg", [B.MSG_FP32, B.MSG_INT8])
+def test_jit_and_generic_kernels_agree(torch_cuda, msg, monkeypatch):
+    # the run-time specialised kernel and the precompiled kernel compute the same
+    # decoder: INT8 sums are exact integers (bit-exact), FP32 differs only in the
+    # association of the c2v sums
+    n, k = 63, 36
+    c = code(n, k)
+    assert c.kernel_info(msg) == "jit"
+    F = 2000
+    cw, llr = frames(n, k, F, 2.0, 1234, ld=64)
+    autos = O.draw_autos(n, 3, 77, 0, F)
+    a = run_nms(torch_cuda, c, llr, autos, 12, 0.78, msg=msg)
+    monkeypatch.setenv("BCHDEC_NMS_KERNEL", "generic")
+    assert c.kernel_info(msg).startswith("generic")
+    b = run_nms(torch_cuda, c, llr, autos, 12, 0.78, msg=msg)
+    if msg == B.MSG_INT8:
+        for key in ("hard", "iters", "flags", "y"):
+            assert np.array_equal(a[key], b[key]), key
+    else:
+        ref = O.nms_enhanced(c.dense(), llr, autos, 12, 0.78, trace=True, threads=None)
+        ok = ~ambiguous_frames(llr, ref, n)
+        assert np.array_equal(a["hard"][ok], b["hard"][ok])
+        assert np.array_equal(a["iters"][ok], b["iters"][ok])

@@ -1,0 +1,78 @@
+"""GPU parity of the reduced-precision message formats against the quantised oracle.
+
+INT8 (with and without power-of-two renormalisation): every quantiser input is an
+exact integer combination or a correctly-rounded division whose .5 ties are exact, so
+hard decisions, iteration counts and final values are bit-exact on every frame.
+FP16: the FP32 accumulation of binary16 messages decides rare binary16 roundings
+differently from the oracle's exact sums; the first iteration is compared within one
+binary16 ulp and full decodes must agree on >= 99% of frames.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import autos_dev, frames, to_dev
+from paper_2412_20828_gb300 import bchdec as B
+
+pytestmark = pytest.mark.gpu
+
+ALPHA = float(np.float32(0.78))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2412_20828_gb300 import build
+    build.build()
+    B.load()
+    return torch
+
+
+def decode(torch, c, llr, autos, iters, msg, rescale, early_stop=True):
+    F, ld = llr.shape
+    p = B.params(iters, ALPHA, n_autos=autos.shape[1], early_stop=early_stop, msg=msg,
+                 rescale=rescale)
+    hard = torch.zeros((F, (c.n + 63) // 64), dtype=torch.int64, device="cuda")
+    it = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    fl = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    yo = torch.zeros((F, ld), dtype=torch.float32, device="cuda")
+    B.nms_decode(c, p, to_dev(llr), autos_dev(autos), hard, it, fl, yo)
+    torch.cuda.synchronize()
+    return dict(hard=B.unpack_bits(hard.cpu().numpy(), c.n), iters=it.cpu().numpy(),
+                flags=fl.cpu().numpy(), y=yo.cpu().numpy()[:, :c.n])
+
+
+@pytest.mark.parametrize("nk", [(63, 36), (63, 45), (127, 64), (127, 99)])
+@pytest.mark.parametrize("rescale", [False, True])
+def test_int8_bit_exact(torch_cuda, nk, rescale):
+    n, k = nk
+    c = B.Code(n, k)
+    F = 800
+    cw, llr = frames(n, k, F, 2.5, 900 + n + k, ld=(n + 3) & ~3)
+    autos = O.draw_autos(n, 3, 31, 0, F)
+    g = decode(torch_cuda, c, llr, autos, 12, B.MSG_INT8, rescale)
+    ref = O.nms_enhanced_q(c.dense(), llr, autos, 12, ALPHA, 2, rescale=rescale, threads=None)
+    assert np.array_equal(g["iters"], ref["iters"])
+    assert np.array_equal(g["hard"], ref["hard"])
+    assert np.array_equal(g["flags"] & 1, ref["converged"])
+    assert np.array_equal(g["y"].astype(np.float64), ref["y"])
+
+
+@pytest.mark.parametrize("nk", [(63, 45), (127, 64)])
+@pytest.mark.parametrize("rescale", [False, True])
+def test_fp16_close_to_oracle(torch_cuda, nk, rescale):
+    n, k = nk
+    c = B.Code(n, k)
+    F = 800
+    cw, llr = frames(n, k, F, 2.5, 950 + n + k, ld=(n + 3) & ~3)
+    autos = O.draw_autos(n, 3, 37, 0, F)
+    # first iteration: within one binary16 ulp of the oracle
+    g1 = decode(torch_cuda, c, llr, autos, 1, B.MSG_FP16, rescale, early_stop=False)
+    r1 = O.nms_enhanced_q(c.dense(), llr, autos, 1, ALPHA, 1, rescale=rescale, early_stop=False)
+    ulp = np.array([O.q16(abs(v) * (1 + 2 ** -10)) - O.q16(abs(v)) if v != 0 else 2 ** -24
+                    for v in r1["y"].ravel()]).reshape(r1["y"].shape)
+    assert np.all(np.abs(g1["y"] - r1["y"]) <= np.maximum(ulp, 2 ** -24) * 1.0001)
+    g = decode(torch_cuda, c, llr, autos, 12, B.MSG_FP16, rescale)
+    ref = O.nms_enhanced_q(c.dense(), llr, autos, 12, ALPHA, 1, rescale=rescale, threads=None)
+    agree = np.all(g["hard"] == ref["hard"], axis=1) & (g["iters"] == ref["iters"])
+    assert agree.mean() >= 0.99

@@ -345,3 +345,40 @@ def test_train_grad_matches_central_differences():
         step = float(lp[f, i]) - float(lm[f, i])
         fd = (O.train_grad(Ho, lp, aut, iters, alpha, cw)[0] - O.train_grad(Ho, lm, aut, iters, alpha, cw)[0]) / step
         assert dl[f, i] == pytest.approx(fd, rel=2e-3, abs=1e-9)
+
+
+# ------------------------------------------------------------------ precision formats
+def test_q16_matches_ieee_binary16():
+    rng = np.random.default_rng(3)
+    xs = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-9, 5, 20000),
+                         [0.0, 65504.0, -65504.0, 6.1e-5, 5.96e-8, 2049.0, 2051.0, 0.1]])
+    for x in xs:
+        exp = float(np.float16(x)) if abs(x) < 65504 else np.sign(x) * 65504.0
+        assert O.q16(x) == exp, x
+
+
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_quantised_decoder_equals_fp64_on_exact_inputs(fmt):
+    # With alpha = 0.5 (P = 1, identity automorphism) and inputs that are multiples of
+    # the format's step within range, every quantiser in the first iteration is exact
+    # (minima of representable values times 1/2 stay representable, up to the integer
+    # rounding of INT8 which is exact on even minima), so the quantised decoder must
+    # reproduce the FP64 decoder.
+    n, k = 15, 7
+    Ho = O.build_ho(n, k)
+    rng = np.random.default_rng(fmt)
+    if fmt == 1:
+        llr = rng.integers(-40, 41, (50, n)).astype(np.float32)
+    else:
+        llr = (rng.integers(-3, 4, (50, n)) * 2).astype(np.float32) / 4.0 * 2.0  # q even
+    llr[llr == 0] = 1.0
+    aut = np.zeros((50, 1), np.uint16)
+    a = O.nms_enhanced_q(Ho, llr, aut, 1, 0.5, fmt, early_stop=False)
+    b = O.nms_enhanced(Ho, llr, aut, 1, 0.5, early_stop=False)
+    if fmt == 1:
+        assert np.array_equal(a["y"], b["y"])
+    else:
+        # INT8 stores 4x clamped to +-31: compare where the FP64 result is in range
+        inr = np.abs(b["y"]) * 4 <= 31
+        assert np.array_equal(a["y"][inr], b["y"][inr])
+    assert np.array_equal(a["hard"], b["hard"])
