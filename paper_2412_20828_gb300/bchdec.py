@@ -25,7 +25,8 @@ FLAG_CONVERGED, FLAG_OSD = 1, 2
 EXPORTS = (
     "bch_build_pcm", "bch_build_pcm_host", "bch_nms_kernel_info", "bch_code_info", "bch_pcm_export", "bch_code_free",
     "bch_draw_automorphisms", "bch_draw_automorphisms_host", "bch_gen_frames",
-    "bch_workspace_size", "bch_nms_decode", "bch_hybrid_decode", "bch_osd_decode",
+    "bch_workspace_size", "bch_nms_decode", "bch_hybrid_decode", "bch_hybrid_decode_noalloc",
+    "bch_osd_decode",
     "bch_compact_failed", "bch_count_errors", "bch_nms_forward_train", "bch_nms_backward", "bch_bce_loss",
     "bch_train_alpha", "bch_decoder_create", "bch_decoder_run_host", "bch_decoder_destroy",
     "bch_status_str", "bch_last_error", "bch_version",
@@ -81,6 +82,8 @@ def load():
             "bch_nms_decode": (st, [P, C.POINTER(NmsParams), P, i, i, P, P, P, P, P, P, P]),
             "bch_hybrid_decode": (st, [P, P, C.POINTER(NmsParams), P, i, i, P, P, P, P, P, P, P,
                                        P, P]),
+            "bch_hybrid_decode_noalloc": (st, [P, P, C.POINTER(NmsParams), P, i, i, P, P, P, P, P,
+                                               P]),
             "bch_osd_decode": (st, [P, i, P, i, P, P, i, P, P, P, P]),
             "bch_compact_failed": (st, [P, i, P, P, P, P]),
             "bch_count_errors": (st, [i, P, P, P, P, i, P, P]),
@@ -264,6 +267,19 @@ def hybrid_decode(code: Code, std_code: Code, p: NmsParams, llr, autos, hard, it
                                     _ptr(autos), _ptr(hard), _ptr(iters), _ptr(flags),
                                     _ptr(llr_out), _ptr(failed_list), _ptr(failed_count), _ptr(ws),
                                     _stream(stream)), "bch_hybrid_decode")
+
+
+def hybrid_decode_noalloc(code: Code, std_code: Code, p: NmsParams, llr, autos, hard, iters, flags,
+                          llr_out=None, stream=None):
+    """bch_hybrid_decode without a workspace: for callers that cannot allocate device
+    memory while decoding (scratch is a fixed ~1 MB device array; n_frames <= 262144)."""
+    import torch
+    _dev(llr, torch.float32, "llr")
+    F, ld = llr.shape
+    _check(load().bch_hybrid_decode_noalloc(code.handle, std_code.handle, C.byref(p), _ptr(llr), ld,
+                                            F, _ptr(autos), _ptr(hard), _ptr(iters), _ptr(flags),
+                                            _ptr(llr_out), _stream(stream)),
+           "bch_hybrid_decode_noalloc")
 
 
 def osd_decode(std_code: Code, order, llr, frame_list, count, hard, flags=None, ws=None,

@@ -1,0 +1,128 @@
+// bch_hybrid_decode_noalloc: the hybrid decoder for callers that cannot allocate device
+// memory at decode time -- code running where cudaMalloc is forbidden or too costly
+// after start-up (real-time receive loops, plug-ins handed only pre-registered
+// buffers, hosts that must not grow the device heap).  The scratch that
+// bch_hybrid_decode takes from a caller-provided workspace (frame-queue counters,
+// per-block failure counts, the failed-frame list and its count) lives here in one
+// file-scope __device__ array instead.  Only precompiled kernels are launched (no
+// run-time compilation, so no module is loaded during a call).
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "bch_kernels.cuh"
+
+using namespace bchlib;
+
+namespace {
+
+constexpr int kNoallocMaxFrames = 262144;
+constexpr size_t kQueueOff = 0;                                          // 2 x u32 queue counters
+constexpr size_t kCountsOff = 256;                                       // u32 per 1024 frames
+constexpr size_t kListOff = kCountsOff + 4096;                           // u32[kNoallocMaxFrames]
+constexpr size_t kCountOff = kListOff + size_t(kNoallocMaxFrames) * 4;  // u32 failed count
+constexpr size_t kScratchBytes = kCountOff + 256;
+
+// Every GPU that loads the library holds this array until the process exits.  In host
+// code its name is only a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress, looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {};
+
+bch_status scratch_address(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(BCH_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(BCH_ECUDA, std::string("cudaGetSymbolAddress of the no-allocation scratch: ") +
+                                 cudaGetErrorString(e));
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return BCH_OK;
+}
+
+}  // namespace
+
+extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_code *std_code,
+                                                const bch_nms_params *p, const float *llr, int ld,
+                                                int n_frames, const uint16_t *autos, uint64_t *hard,
+                                                uint8_t *iters, uint8_t *flags, float *llr_out,
+                                                void *stream) {
+  if (!code || !code->dev_dc || !std_code || !std_code->dev_dc) return fail(BCH_EINVAL, "null code");
+  if (std_code->kind != BCH_PCM_STANDARD || std_code->alg.n != code->alg.n || std_code->alg.k != code->alg.k)
+    return fail(BCH_EINVAL, "std_code must be the standard matrix of the same code");
+  if (!p || !p->alpha || p->iters < 1 || p->iters > 32 || p->n_autos < 1 || p->n_autos > 9 ||
+      p->msg < BCH_MSG_FP32 || p->msg > BCH_MSG_INT8 || p->osd_order < 0 || p->osd_order > 2)
+    return fail(BCH_EINVAL, "bad decoder parameters");
+  if (n_frames < 0 || ld < code->alg.n) return fail(BCH_EINVAL, "bad frame layout");
+  if (n_frames > kNoallocMaxFrames)
+    return fail(BCH_EINVAL, "n_frames exceeds the 262144 frames the no-allocation scratch holds; "
+                            "split the batch or use bch_hybrid_decode with a workspace");
+  if (n_frames == 0) return BCH_OK;
+  if (!llr || !autos || !hard || !flags) return fail(BCH_EINVAL, "null buffer");
+  void *base = nullptr;
+  bch_status s = scratch_address(&base);
+  if (s != BCH_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char *ws = static_cast<unsigned char *>(base);
+  unsigned *queue = reinterpret_cast<unsigned *>(ws + kQueueOff);
+  // the array keeps the previous call's contents: the queue counters must start at 0
+  cudaError_t e = cudaMemsetAsync(queue, 0, 16, st);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("clear scratch: ") + cudaGetErrorString(e));
+
+  NmsArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.dc = code->dc;
+  a.llr = llr;
+  a.ld = ld;
+  a.F = n_frames;
+  a.autos = autos;
+  a.P = p->n_autos;
+  a.hard = hard;
+  a.iters = iters;
+  a.flags = flags;
+  a.llr_out = llr_out;
+  a.queue = queue;
+  a.I = p->iters;
+  a.early_stop = p->early_stop ? 1 : 0;
+  a.msg = int(p->msg);
+  a.rescale = p->rescale ? 1 : 0;
+  for (int t = 0; t < 32; t++) a.alpha[t] = t < p->iters ? p->alpha[t] : 0.0f;
+  e = launch_nms(a, st);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("nms kernel: ") + cudaGetErrorString(e));
+
+  uint32_t *counts = reinterpret_cast<uint32_t *>(ws + kCountsOff);
+  uint32_t *list = reinterpret_cast<uint32_t *>(ws + kListOff);
+  uint32_t *count = reinterpret_cast<uint32_t *>(ws + kCountOff);
+  e = launch_compact(flags, n_frames, counts, list, count, st);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("compaction: ") + cudaGetErrorString(e));
+
+  const int n = std_code->alg.n, M = n - std_code->alg.k;
+  if (M > 64) return fail(BCH_EINVAL, "OSD supports n-k <= 64");
+  OsdArgs o;
+  o.n = n;
+  o.k = std_code->alg.k;
+  o.M = M;
+  o.rows = reinterpret_cast<const uint4 *>(std_code->dc.rowmask);
+  o.llr = llr;
+  o.ld = ld;
+  o.list = list;
+  o.count = count;
+  o.max_frames = n_frames;
+  o.order = p->osd_order;
+  o.hard = hard;
+  o.flags = flags;
+  o.queue = queue + 1;
+  e = launch_osd(o, st);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("osd kernel: ") + cudaGetErrorString(e));
+  return BCH_OK;
+}
