@@ -156,6 +156,43 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+SERVE_CODES = [(63, 36), (63, 45), (127, 64), (127, 99)]
+
+
+def run_serving(B, torch, dev, seconds, rate):
+    """Config 5: Poisson arrivals (rate req/s), 1..4096 frames (log-uniform), code uniform
+    over four BCH codes, Eb/N0 uniform in [1, 6] dB per frame; latency = arrival -> results
+    in host memory.  The same stream is run through the server (continuous batching in a
+    persistent kernel, 16 GB budget) and through static batching (collect 1 ms or 64k
+    frames, one hybrid decode per code, copy back)."""
+    codes = [B.Code(n, k) for n, k in SERVE_CODES]
+    stds = [B.Code(n, k, kind=B.PCM_STANDARD) for n, k in SERVE_CODES]
+    pools = []
+    pool_frames = 262144
+    for c in codes:
+        ld = (c.n + 3) & ~3
+        d = torch.empty((pool_frames, ld), dtype=torch.float32, device=dev)
+        B.gen_frames(c, 1.0, 6.0, 777 + c.n + c.k, 0, d)
+        h = torch.empty((pool_frames, ld), dtype=torch.float32, pin_memory=True)
+        h.copy_(d.cpu())
+        pools.append(h)
+    torch.cuda.synchronize()
+    srv = B.Server(codes, stds, ITERS, ALPHA, n_autos=P_AUTOS, osd_order=OSD_ORDER,
+                   budget_bytes=16 << 30, max_requests=8192, max_frames_per_request=4096)
+    # warm-up: a short stream
+    B.serve_bench(srv, codes, stds, pools, rate, 0.5, seed=11)
+    res = B.serve_bench(srv, codes, stds, pools, rate, seconds, seed=12)
+    stats = srv.stats()
+    srv.close()
+    stat = B.serve_bench(None, codes, stds, pools, rate, seconds, seed=12, static_batching=True,
+                         batch_us=1000, batch_frames=65536)
+    return {"workload": f"Poisson {rate:.0f} req/s, 1-4096 frames log-uniform, codes "
+                        "(63,36),(63,45),(127,64),(127,99), Eb/N0 U[1,6] dB, hybrid NMS(12,P=3)+OSD(2)",
+            "seconds": seconds, "server": res, "server_stats": stats,
+            "static_batching": stat}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -169,6 +206,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--msg", default="fp32", choices=["fp32", "fp16", "int8"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="duration of the serving stream (0 skips serving)")
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -300,9 +340,11 @@ def main():
     clk_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_lane_ops = sms * 128 * clk_mhz * 1e6
     achieved = edge_updates * LANE_OPS_PER_EDGE / nms_time
+    kinfo = states[0]["code"].kernel_info(msg, P_AUTOS)
+    kname = "bch_nms_jit" if kinfo == "jit" else "nms_enhanced_kernel"
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lane_ops / 1e12,
                 "unit": "Tlane-op/s", "frac": achieved / peak_lane_ops, "traffic": None,
-                "kernel": "nms_enhanced_kernel", "lane_ops_per_edge_update": LANE_OPS_PER_EDGE,
+                "kernel": kname, "kernel_info": kinfo, "lane_ops_per_edge_update": LANE_OPS_PER_EDGE,
                 "edge_updates_per_s": eups, "nms_ms_per_step": nms_time * 1e3,
                 "peak_basis": f"{sms} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock under load)"}
 
@@ -335,6 +377,11 @@ def main():
                "d2h_bytes_per_step": int(frames_per_step * (8 + 2))}
         for d in dec:
             d.close()
+
+    # ---- serving: mixed-code Poisson stream, server vs static batching
+    serving = None
+    if rank == 0 and args.serve_seconds > 0:
+        serving = run_serving(B, torch, dev, args.serve_seconds, args.serve_rate)
 
     # ---- CPU baseline: the oracle on a bounded sample, and FER agreement
     cpu = None
@@ -369,6 +416,7 @@ def main():
                        "parallelism": f"frames sharded over {world} GPU(s)"},
             "edge_updates_per_s": eups, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": args.steps * len(CODES) * (NPT + 1 + 2 + 1 + NPT),
+            "serving": serving,
             "fer_match_oracle_ci95": fer_match, "per_point": per_point,
         }
         print(json.dumps(line), flush=True)

@@ -258,6 +258,85 @@ bch_status bch_decoder_run_host(bch_decoder *dec, const float *llr, int n_frames
                                 uint8_t *iters, uint8_t *flags);
 void bch_decoder_destroy(bch_decoder *dec);
 
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous-batching decode server.  Requests (one code, 1..max frames each) are
+ * admitted as device slots as HBM (budget_bytes) and slots (max_requests) free up and
+ * are decoded by the hybrid decoder (enhanced NMS, OSD on the frames it fails when
+ * std_codes[i] is given) inside a persistent kernel, overlapping requests that are
+ * already on the GPU.  Per-frame results do not depend on which other requests are
+ * in flight.  All device waits are bounded: an idle kernel exits after idle_exit_us
+ * (default 200 ms) and is relaunched on demand. */
+typedef struct bch_server bch_server;
+typedef struct {
+  int n_codes;                           /* 1..8 code ids                              */
+  const bch_code *const *codes;          /* [n_codes] matrices for NMS (H_o)           */
+  const bch_code *const *std_codes;      /* [n_codes] standard H for OSD, or NULL      */
+  int iters;                             /* I_m                                         */
+  const float *alpha;                    /* [iters], copied                             */
+  int n_autos;                           /* P                                           */
+  int osd_order;                         /* 0..2                                        */
+  size_t budget_bytes;                   /* HBM for request data (LLR, draws, results) */
+  int max_requests;                      /* slots (requests in flight), <= 65535        */
+  int max_frames_per_request;            /* 0: no limit beyond the budget               */
+  int warps;                             /* persistent warps; 0: fill the GPU           */
+  unsigned idle_exit_us;                 /* idle time before the kernel exits           */
+} bch_server_config;
+
+typedef struct {
+  long long submitted, admitted, queued, completed, kernel_launches;
+  long long bytes_in_use, pending, in_flight;
+} bch_server_stats;
+
+bch_status bch_server_create(const bch_server_config *cfg, bch_server **out);
+/* Submits a request: llr [n_frames][ld] FP32 (host or device memory; it must stay
+ * valid until the request completes), automorphisms drawn from (autos_seed, frame0 +
+ * index).  Admitted at once when memory and a slot are free, else queued in FIFO
+ * order; BCH_EBUDGET if it can never fit the budget.  *request_id identifies it. */
+bch_status bch_server_submit(bch_server *srv, int code_id, const float *llr, int ld,
+                             int n_frames, uint64_t autos_seed, uint64_t frame0,
+                             uint64_t *request_id);
+/* Collects up to max_ids completed request ids (waiting up to timeout_us for at least
+ * one) and admits queued requests that now fit. */
+bch_status bch_server_poll(bch_server *srv, uint64_t *done_ids, int max_ids, int *n_done,
+                           int timeout_us);
+/* Copies a completed request's results to caller memory (hard [n][ceil(n/64)], iters,
+ * flags; host or device) and releases its memory and slot. */
+bch_status bch_server_fetch(bch_server *srv, uint64_t request_id, uint64_t *hard,
+                            uint8_t *iters, uint8_t *flags);
+bch_status bch_server_get_stats(bch_server *srv, bch_server_stats *out);
+/* Stops the kernel (at its next chunk boundary) and frees everything. */
+void bch_server_destroy(bch_server *srv);
+
+/* Serving benchmark (open loop).  Poisson arrivals at rate_rps for duration_s; each
+ * request: code uniform over n_codes, size floor(exp(u ln(max_frames+1))) clipped to
+ * [1, max_frames], frames = a contiguous range of that code's host frame pool.
+ * Latency = scheduled arrival -> results in host memory.  static_batching = 1 sends the
+ * same stream through plain batched launches (collect for batch_us after the first
+ * request or batch_frames frames, one bch_hybrid_decode per code, copy back) instead of
+ * the server (srv may then be NULL). */
+typedef struct {
+  double rate_rps, duration_s;
+  int max_frames;
+  uint64_t seed;
+  int n_codes;
+  const float *const *pools;  /* [n_codes] host frame pools [pool_frames][ld]            */
+  const int *pool_frames;     /* [n_codes]                                               */
+  const int *lds;             /* [n_codes]                                               */
+  const bch_code *const *codes, *const *std_codes; /* used by static batching            */
+  int iters; const float *alpha; int n_autos; int osd_order; /* static batching decoder */
+  int static_batching, batch_us, batch_frames;
+} bch_serve_bench_config;
+
+typedef struct {
+  long long requests, frames;
+  double p50_ms, p99_ms, mean_ms, max_ms, elapsed_s;
+  double served_frames_per_s, offered_frames_per_s, offered_requests_per_s;
+} bch_serve_bench_result;
+
+bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *cfg,
+                           bch_serve_bench_result *res);
+
 /* ---------------------------------------------------------------- training */
 
 /* Training forward pass: all `iters` iterations without early stop (FP32 only),

@@ -822,7 +822,8 @@ static int row_vars(const uint8_t *H, int n, int r, int *vars) {
  * decision); hard decision c_i = [x_i < 0]; stop when H c^T = 0 (if early_stop) or
  * after `iters` iterations.  Outputs per frame: hard bits (bytes), iterations run,
  * converged flag, final x (double), the largest operand magnitude met (|L| + sum of
- * |c2v| over a variable's edges) and the smallest |v2c| or |x| relative to it. */
+ * |c2v| over a variable's edges) and the smallest |v2c| or |x| relative to its own
+ * operand magnitude (a sign decided by rounding order shows as a tiny ratio). */
 int or_nms_plain(const uint8_t *H, int M, int n, const float *llr, int ld, int F, int iters,
                  double alpha, int early_stop, uint8_t *hard, int *iters_used,
                  uint8_t *converged, double *y_out, double *env_out, double *margin_out) {
@@ -845,13 +846,18 @@ int or_nms_plain(const uint8_t *H, int M, int n, const float *llr, int ld, int F
     }
     for (int t = 1; t <= iters; t++) {
       /* Eq. (2) */
+      double tmar = INFINITY;
       for (int j = 0; j < M; j++)
         for (int i = 0; i < n; i++) {
           if (!H[j * n + i]) continue;
-          double s = (double)L[i];
+          double s = (double)L[i], sa = fabs((double)L[i]);
           for (int kk = 0; kk < M; kk++)
-            if (kk != j && H[kk * n + i]) s += c2v[kk * n + i];
+            if (kk != j && H[kk * n + i]) {
+              s += c2v[kk * n + i];
+              sa += fabs(c2v[kk * n + i]);
+            }
           v2c[j * n + i] = s;
+          if (fabs(s) / sa < tmar) tmar = fabs(s) / sa;
         }
       /* Eq. (3) */
       for (int j = 0; j < M; j++) {
@@ -861,21 +867,19 @@ int or_nms_plain(const uint8_t *H, int M, int n, const float *llr, int ld, int F
       }
       memcpy(c2v, nc2v, sizeof(double) * (size_t)M * n);
       /* Eq. (4) */
-      double tmar = INFINITY;
       for (int i = 0; i < n; i++) {
         double s = (double)L[i], sa = fabs((double)L[i]);
         for (int j = 0; j < M; j++)
           if (H[j * n + i]) {
             s += c2v[j * n + i];
             sa += fabs(c2v[j * n + i]);
-            if (fabs(v2c[j * n + i]) < tmar) tmar = fabs(v2c[j * n + i]);
           }
         x[i] = s;
         c[i] = s < 0.0;
         if (sa > env) env = sa;
-        if (fabs(s) < tmar) tmar = fabs(s);
+        if (fabs(s) / sa < tmar) tmar = fabs(s) / sa;
       }
-      if (tmar / env < mar) mar = tmar / env;
+      if (tmar < mar) mar = tmar;
       t_run = t;
       ok = or_syndrome_weight(H, M, n, c) == 0;
       if (early_stop && ok) break;

@@ -29,6 +29,8 @@ EXPORTS = (
     "bch_osd_decode",
     "bch_compact_failed", "bch_count_errors", "bch_nms_forward_train", "bch_nms_backward", "bch_bce_loss",
     "bch_train_alpha", "bch_decoder_create", "bch_decoder_run_host", "bch_decoder_destroy",
+    "bch_server_create", "bch_server_submit", "bch_server_poll", "bch_server_fetch",
+    "bch_server_get_stats", "bch_server_destroy", "bch_serve_bench",
     "bch_status_str", "bch_last_error", "bch_version",
 )
 
@@ -42,6 +44,38 @@ class BchError(RuntimeError):
 class PcmOpts(C.Structure):
     _fields_ = [("q_rounds", C.c_int), ("sa_steps", C.c_int), ("sa_lambda", C.c_double),
                 ("sa_t0_frac", C.c_double), ("sa_cool", C.c_double)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("n_codes", C.c_int), ("codes", C.POINTER(C.c_void_p)),
+                ("std_codes", C.POINTER(C.c_void_p)), ("iters", C.c_int),
+                ("alpha", C.POINTER(C.c_float)), ("n_autos", C.c_int), ("osd_order", C.c_int),
+                ("budget_bytes", C.c_size_t), ("max_requests", C.c_int),
+                ("max_frames_per_request", C.c_int), ("warps", C.c_int),
+                ("idle_exit_us", C.c_uint)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(nm, C.c_longlong) for nm in ("submitted", "admitted", "queued", "completed",
+                                               "kernel_launches", "bytes_in_use", "pending",
+                                               "in_flight")]
+
+
+class ServeBenchConfig(C.Structure):
+    _fields_ = [("rate_rps", C.c_double), ("duration_s", C.c_double), ("max_frames", C.c_int),
+                ("seed", C.c_uint64), ("n_codes", C.c_int), ("pools", C.POINTER(C.c_void_p)),
+                ("pool_frames", C.POINTER(C.c_int)), ("lds", C.POINTER(C.c_int)),
+                ("codes", C.POINTER(C.c_void_p)), ("std_codes", C.POINTER(C.c_void_p)),
+                ("iters", C.c_int), ("alpha", C.POINTER(C.c_float)), ("n_autos", C.c_int),
+                ("osd_order", C.c_int), ("static_batching", C.c_int), ("batch_us", C.c_int),
+                ("batch_frames", C.c_int)]
+
+
+class ServeBenchResult(C.Structure):
+    _fields_ = [("requests", C.c_longlong), ("frames", C.c_longlong), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("elapsed_s", C.c_double), ("served_frames_per_s", C.c_double),
+                ("offered_frames_per_s", C.c_double), ("offered_requests_per_s", C.c_double)]
 
 
 class NmsParams(C.Structure):
@@ -94,6 +128,13 @@ def load():
             "bch_decoder_create": (st, [P, P, C.POINTER(NmsParams), i, i, C.POINTER(P)]),
             "bch_decoder_run_host": (st, [P, P, i, u64, u64, P, P, P]),
             "bch_decoder_destroy": (None, [P]),
+            "bch_server_create": (st, [C.POINTER(ServerConfig), C.POINTER(P)]),
+            "bch_server_submit": (st, [P, i, P, i, i, u64, u64, C.POINTER(u64)]),
+            "bch_server_poll": (st, [P, P, i, C.POINTER(i), i]),
+            "bch_server_fetch": (st, [P, u64, P, P, P]),
+            "bch_server_get_stats": (st, [P, C.POINTER(ServerStats)]),
+            "bch_server_destroy": (None, [P]),
+            "bch_serve_bench": (st, [P, C.POINTER(ServeBenchConfig), C.POINTER(ServeBenchResult)]),
             "bch_status_str": (C.c_char_p, [i]),
             "bch_last_error": (C.c_char_p, []),
             "bch_version": (C.c_char_p, []),
@@ -365,6 +406,92 @@ class HostDecoder:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """bch_server: continuous-batching hybrid decoding of requests of mixed codes."""
+
+    def __init__(self, codes, std_codes, iters, alpha, n_autos=3, osd_order=2,
+                 budget_bytes=16 << 30, max_requests=1024, max_frames_per_request=4096, warps=0,
+                 idle_exit_us=200000):
+        self.codes, self.std_codes = list(codes), list(std_codes) if std_codes else None
+        self._al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float32), (iters,)))
+        n = len(self.codes)
+        self._ch = (C.c_void_p * n)(*[c.handle.value for c in self.codes])
+        self._sh = (C.c_void_p * n)(*[c.handle.value if c else None for c in self.std_codes]) \
+            if self.std_codes else None
+        cfg = ServerConfig(n, C.cast(self._ch, C.POINTER(C.c_void_p)),
+                           C.cast(self._sh, C.POINTER(C.c_void_p)) if self._sh else None,
+                           iters, self._al.ctypes.data_as(C.POINTER(C.c_float)), n_autos, osd_order,
+                           budget_bytes, max_requests, max_frames_per_request, warps, idle_exit_us)
+        self._h = C.c_void_p()
+        _check(load().bch_server_create(C.byref(cfg), C.byref(self._h)), "bch_server_create")
+        self._keep = {}
+
+    def submit(self, code_id, llr, autos_seed, frame0):
+        """llr: [F, ld] FP32 numpy array (host) or CUDA tensor; kept alive until fetched."""
+        F, ld = llr.shape
+        rid = C.c_uint64()
+        _check(load().bch_server_submit(self._h, code_id, _ptr(llr), ld, F, autos_seed, frame0,
+                                        C.byref(rid)), "bch_server_submit")
+        self._keep[rid.value] = (llr, code_id, F)
+        return rid.value
+
+    def poll(self, max_ids=256, timeout_us=0):
+        ids = np.zeros(max_ids, np.uint64)
+        nd = C.c_int()
+        _check(load().bch_server_poll(self._h, _ptr(ids), max_ids, C.byref(nd), timeout_us),
+               "bch_server_poll")
+        return [int(x) for x in ids[: nd.value]]
+
+    def fetch(self, rid):
+        llr, code_id, F = self._keep.pop(rid)
+        n = self.codes[code_id].n
+        hard = np.zeros((F, (n + 63) // 64), np.uint64)
+        it = np.zeros(F, np.uint8)
+        fl = np.zeros(F, np.uint8)
+        _check(load().bch_server_fetch(self._h, rid, _ptr(hard), _ptr(it), _ptr(fl)),
+               "bch_server_fetch")
+        return hard.view(np.int64), it, fl
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().bch_server_get_stats(self._h, C.byref(st)), "bch_server_get_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            load().bch_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def serve_bench(server, codes, std_codes, pools, rate_rps, duration_s, max_frames=4096, seed=1,
+                iters=12, alpha=0.78, n_autos=3, osd_order=2, static_batching=False,
+                batch_us=1000, batch_frames=65536):
+    """bch_serve_bench: pools are pinned host tensors / numpy arrays [pool_frames, ld]."""
+    n = len(pools)
+    al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float32), (iters,)))
+    pp = (C.c_void_p * n)(*[_ptr(p).value for p in pools])
+    pf = (C.c_int * n)(*[int(p.shape[0]) for p in pools])
+    ld = (C.c_int * n)(*[int(p.shape[1]) for p in pools])
+    ch = (C.c_void_p * n)(*[c.handle.value for c in codes])
+    sh = (C.c_void_p * n)(*[c.handle.value for c in std_codes]) if std_codes else None
+    cfg = ServeBenchConfig(rate_rps, duration_s, max_frames, seed, n,
+                           C.cast(pp, C.POINTER(C.c_void_p)), pf, ld,
+                           C.cast(ch, C.POINTER(C.c_void_p)),
+                           C.cast(sh, C.POINTER(C.c_void_p)) if sh else None, iters,
+                           al.ctypes.data_as(C.POINTER(C.c_float)), n_autos, osd_order,
+                           int(static_batching), batch_us, batch_frames)
+    res = ServeBenchResult()
+    _check(load().bch_serve_bench(server._h if server else None, C.byref(cfg), C.byref(res)),
+           "bch_serve_bench")
+    return {k: getattr(res, k) for k, _ in ServeBenchResult._fields_}
 
 
 def unpack_bits(words: np.ndarray, n: int) -> np.ndarray:

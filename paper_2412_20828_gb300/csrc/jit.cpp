@@ -71,36 +71,48 @@ NvrtcApi &nvrtc() {
   return api;
 }
 
-// Per-format definitions of the row macros used by the generated rows.
+// Per-format definitions of the row macros used by the generated rows.  Within one
+// automorphism z is fixed, so c2v(j,u) = sg_j sgn(z_u) alpha m_j(u) with sg_j the sign
+// product of the whole row: the rows accumulate T[u] = sum_j sg_j alpha m_j(u) and the
+// factor sgn(z_u) is applied once per variable at the end.  sg_j is the parity of the
+// row's negative entries, taken from the copy's sign mask with the row mask as an
+// immediate.  m_j(u) is min1 except at the row's minimum, handled by a predicated add
+// of (v2 - v1) -- this keeps min/max/compare work on the ALU pipe down to ~4 operations
+// per edge and moves the additions to the FMA pipe.
 const char *row_macros(int msg) {
   if (msg == 2)
     return R"(
 #define BCH_VT int
-#define BCH_R0 { int m1_ = 1 << 20, m2_ = 1 << 20, a_; uint32_t sg_ = 0u;
-#define BCH_R1(u) a_ = abs(z[u]); m2_ = min(m2_, max(m1_, a_)); m1_ = min(m1_, a_); sg_ ^= uint32_t(z[u]);
-#define BCH_RM const int c1_ = __double2int_rn(double(alpha) * double(m1_)); \
+#define BCH_R0 { int m1_ = 1 << 20, m2_ = 1 << 20, a_;
+#define BCH_R1(u) a_ = abs(z[u]); m2_ = min(m2_, max(m1_, a_)); m1_ = min(m1_, a_);
+#define BCH_RM(SG) const int c1_ = __double2int_rn(double(alpha) * double(m1_)); \
   const int c2_ = __double2int_rn(double(alpha) * double(m2_)); \
-  const int v1_ = (sg_ & kSign) ? -c1_ : c1_; const int v2_ = (sg_ & kSign) ? -c2_ : c2_;
-#define BCH_R2(u) { const int mg_ = (abs(z[u]) == m1_) ? v2_ : v1_; BCH_SV(u) += (z[u] < 0) ? -mg_ : mg_; }
+  const bool neg_ = (SG); const int v1_ = neg_ ? -c1_ : c1_; const int dv_ = (neg_ ? -c2_ : c2_) - v1_;
+#define BCH_R2(u) BCH_SV(u) += v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_RE }
+#define BCH_FIN(u) ((z[u] < 0) ? -BCH_SV(u) : BCH_SV(u))
 )";
   if (msg == 1)
     return R"(
 #define BCH_VT float
-#define BCH_R0 { float m1_ = FLT_MAX, m2_ = FLT_MAX, a_; uint32_t sg_ = 0u;
-#define BCH_R1(u) a_ = fabsf(z[u]); m2_ = fminf(m2_, fmaxf(m1_, a_)); m1_ = fminf(m1_, a_); sg_ ^= __float_as_uint(z[u]);
-#define BCH_RM const float v1_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m1_))), sg_); \
-  const float v2_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m2_))), sg_);
-#define BCH_R2(u) BCH_SV(u) += flip_sign((fabsf(z[u]) == m1_) ? v2_ : v1_, __float_as_uint(z[u]));
+#define BCH_R0 { float m1_ = FLT_MAX, m2_ = FLT_MAX;
+#define BCH_R1(u) m2_ = fminf(m2_, fmaxf(m1_, fabsf(z[u]))); m1_ = fminf(m1_, fabsf(z[u]));
+#define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
+  const float v1_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m1_))), sg_); \
+  const float dv_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m2_))), sg_) - v1_;
+#define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_RE }
+#define BCH_FIN(u) flip_sign(BCH_SV(u), __float_as_uint(z[u]))
 )";
   return R"(
 #define BCH_VT float
-#define BCH_R0 { float m1_ = FLT_MAX, m2_ = FLT_MAX, a_; uint32_t sg_ = 0u;
-#define BCH_R1(u) a_ = fabsf(z[u]); m2_ = fminf(m2_, fmaxf(m1_, a_)); m1_ = fminf(m1_, a_); sg_ ^= __float_as_uint(z[u]);
-#define BCH_RM const float v1_ = flip_sign(alpha * m1_, sg_); const float v2_ = flip_sign(alpha * m2_, sg_);
-#define BCH_R2(u) BCH_SV(u) += flip_sign((fabsf(z[u]) == m1_) ? v2_ : v1_, __float_as_uint(z[u]));
+#define BCH_R0 { float m1_ = FLT_MAX, m2_ = FLT_MAX;
+#define BCH_R1(u) m2_ = fminf(m2_, fmaxf(m1_, fabsf(z[u]))); m1_ = fminf(m1_, fabsf(z[u]));
+#define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
+  const float v1_ = flip_sign(alpha * m1_, sg_); const float dv_ = flip_sign(alpha * m2_, sg_) - v1_;
+#define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_RE }
+#define BCH_FIN(u) flip_sign(BCH_SV(u), __float_as_uint(z[u]))
 )";
 }
 
@@ -115,13 +127,14 @@ std::map<std::string, std::shared_ptr<Compiled>> g_cache;
 
 }  // namespace
 
-int jit_block_size(int n) { return n <= 63 ? 128 : 64; }
+int jit_block_size(int n) { return n <= 63 ? 384 : 64; }
+bool jit_lockstep(int n) { return n <= 63; }
 // Resident blocks per SM the register budget is sized for (3 x 128 threads for n <= 63:
 // at most 170 registers, enough for the 2n register-resident values plus temporaries).
 int jit_min_blocks(int n) {
   const char *v = std::getenv("BCHDEC_JIT_MIN_BLOCKS");  // tuning knob (register budget)
   if (v && std::atoi(v) >= 1 && std::atoi(v) <= 8) return std::atoi(v);
-  return n <= 63 ? 3 : 2;
+  return n <= 63 ? 1 : 2;
 }
 int jit_scratch_words(int n) { return n <= 63 ? 0 : n; }
 
@@ -144,34 +157,51 @@ std::string jit_source(const bch_code *c, int msg) {
   o << "struct JitCopy {\n  static constexpr int kScratch = " << scratch << ";\n"
     << "  __device__ __forceinline__ void operator()(const SmemTables &, int, uint32_t, uint32_t,\n"
     << "      StoreT<" << msg << ">::Y *y, StoreT<" << msg << ">::A *acc, StoreT<" << msg
-    << ">::A *scr, uint32_t jr, uint32_t sp, uint32_t sh, float alpha) const {\n"
+    << ">::A *scr, uint32_t jr, uint32_t sp, uint32_t, float alpha) const {\n"
     << "    BCH_VT z[" << n << "];\n"
     << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) {\n"
     << "      const uint32_t i = addmod(bfe32(uint32_t(u) | (uint32_t(u) << " << m << "), jr, " << m
-    << "), sp, " << n << ");\n      z[u] = ld_y(y + (i << sh));\n    }\n";
+    << "), sp, " << n << ");\n      z[u] = ld_y(y + i * " << tpb << ");\n    }\n";
   if (scratch)
     o << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) BCH_SV(u) = 0;\n";
   else
     o << "    StoreT<" << msg << ">::A S[" << n << "];\n#pragma unroll\n    for (int u = 0; u < " << n
       << "; u++) S[u] = 0;\n";
+  // sign mask of the permuted word: bit u = [z_u < 0]
+  o << "    uint32_t ng[" << nw << "];\n#pragma unroll\n    for (int w = 0; w < " << nw << "; w++) ng[w] = 0u;\n"
+    << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) ng[u >> 5] |= "
+    << (msg == 2 ? "(uint32_t(z[u]) >> 31)" : "(__float_as_uint(z[u]) >> 31)") << " << (u & 31);\n";
   // rows, grouped by weight like the device image
   for (const Row &row : c->rows) {
     std::vector<int> cols;
     for (int u = 0; u < n; u++)
       if (row.get(u)) cols.push_back(u);
+    uint32_t mw[4] = {0, 0, 0, 0};
+    for (int u : cols) mw[u >> 5] |= 1u << (u & 31);
+    std::ostringstream sg;
+    sg << "(__popc(";
+    bool first = true;
+    for (int w = 0; w < nw; w++) {
+      if (!mw[w]) continue;
+      if (!first) sg << " ^ ";
+      sg << "(ng[" << w << "] & 0x" << std::hex << mw[w] << std::dec << "u)";
+      first = false;
+    }
+    sg << ") & 1u)";
     o << "    BCH_R0";
     for (int u : cols) o << " BCH_R1(" << u << ")";
-    o << " BCH_RM";
+    o << " BCH_RM(" << sg.str() << ")";
     for (int u : cols) o << " BCH_R2(" << u << ")";
     o << " BCH_RE\n";
   }
   o << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) {\n"
     << "      const uint32_t i = addmod(bfe32(uint32_t(u) | (uint32_t(u) << " << m << "), jr, " << m
-    << "), sp, " << n << ");\n      acc[i << sh] += BCH_SV(u);\n    }\n  }\n};\n}  // namespace bchlib\n";
+    << "), sp, " << n << ");\n      acc[i * " << tpb << "] += BCH_FIN(u);\n    }\n  }\n};\n}  // namespace bchlib\n";
   o << "extern \"C\" __global__ void __launch_bounds__(" << tpb << ", " << jit_min_blocks(n)
     << ") bch_nms_jit(const bchlib::NmsArgs a) {\n"
     << "  extern __shared__ __align__(16) unsigned char smem[];\n"
-    << "  bchlib::nms_persistent<" << msg << ", " << nw << ">(a, smem, bchlib::JitCopy());\n}\n";
+    << "  bchlib::nms_persistent<" << msg << ", " << nw << ", " << (jit_lockstep(n) ? "true" : "false")
+    << ", " << tpb << ">(a, smem, bchlib::JitCopy());\n}\n";
   return o.str();
 }
 

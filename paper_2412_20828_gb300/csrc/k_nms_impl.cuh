@@ -9,7 +9,7 @@ namespace bchlib {
 template <int MSG, int NW, int WB>
 __global__ void __launch_bounds__(128) nms_enhanced_kernel(const NmsArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  nms_persistent<MSG, NW>(a, smem, GenericCopy<MSG, WB>());
+  nms_persistent<MSG, NW, false, 0>(a, smem, GenericCopy<MSG, WB>());
 }
 
 // ---------------------------------------------------------------- plain NMS

@@ -107,7 +107,7 @@ template <int MSG, int WB>
 __device__ __forceinline__ void enh_rows(const uint16_t *__restrict__ codes, int nrows, int w,
                                       int w4, typename StoreT<MSG>::Y *__restrict__ y,
                                       typename StoreT<MSG>::A *__restrict__ acc, uint32_t jr,
-                                      uint32_t sp, uint32_t n, uint32_t m, uint32_t sh,
+                                      uint32_t sp, uint32_t n, uint32_t m, uint32_t stride,
                                       float alpha) {
   using A = typename StoreT<MSG>::A;
   for (int r = 0; r < nrows; r++) {
@@ -127,7 +127,7 @@ __device__ __forceinline__ void enh_rows(const uint16_t *__restrict__ codes, int
               const uint32_t word = h < 2 ? q.x : q.y;
               const uint32_t rr = bfe32(word, jr + ((h & 1) ? 16u : 0u), m);
               const uint32_t i = addmod(rr, sp, n);
-              ix[e + h] = i << sh;
+              ix[e + h] = i * stride;
               const int v = ld_y(y + ix[e + h]);
               z[e + h] = v;
               const int av = abs(v);
@@ -170,7 +170,7 @@ __device__ __forceinline__ void enh_rows(const uint16_t *__restrict__ codes, int
               const uint32_t word = h < 2 ? q.x : q.y;
               const uint32_t rr = bfe32(word, jr + ((h & 1) ? 16u : 0u), m);
               const uint32_t i = addmod(rr, sp, n);
-              ix[e + h] = i << sh;
+              ix[e + h] = i * stride;
               const float v = ld_y(y + ix[e + h]);
               z[e + h] = v;
               const float av = fabsf(v);
@@ -211,11 +211,11 @@ __device__ __forceinline__ void enh_rows(const uint16_t *__restrict__ codes, int
 template <int MSG, int WB>
 __device__ __forceinline__ void enh_copy(const SmemTables &tb, int n_groups, uint32_t n, uint32_t m,
                                          typename StoreT<MSG>::Y *y, typename StoreT<MSG>::A *acc,
-                                         uint32_t jr, uint32_t sp, uint32_t sh, float alpha) {
+                                         uint32_t jr, uint32_t sp, uint32_t stride, float alpha) {
   for (int g = 0; g < n_groups; g++) {
     const GroupDesc gd = tb.grp[g];
     const int w = gd.w;
-    enh_rows<MSG, WB>(tb.codes + gd.off, gd.rows, w, (w + 3) & ~3, y, acc, jr, sp, n, m, sh, alpha);
+    enh_rows<MSG, WB>(tb.codes + gd.off, gd.rows, w, (w + 3) & ~3, y, acc, jr, sp, n, m, stride, alpha);
   }
 }
 
@@ -296,13 +296,17 @@ __device__ __forceinline__ int pull_frame(unsigned *queue, bool need, int F) {
 // The persistent frame loop shared by the precompiled and the run-time compiled
 // kernels; `copy` processes one automorphism of one frame (check pass + accumulate).
 // Per-thread shared columns (stride = block size): ctx[P], acc[n], y[n], then
-// Copy::kScratch words of scratch for the functor.
-template <int MSG, int NW, class Copy>
+// Copy::kScratch words of scratch for the functor.  TPBC: compile-time block size (0 =
+// blockDim.x).  LOCKSTEP: the block's warps start every automorphism together (a
+// barrier per copy) and lanes without a frame run it on their stale column, so all
+// warps of the block stream through the same code -- for long straight-line copy code
+// this keeps the instruction cache warm.
+template <int MSG, int NW, bool LOCKSTEP, int TPBC, class Copy>
 __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *smem, const Copy &copy) {
   using Y = typename StoreT<MSG>::Y;
   using A = typename StoreT<MSG>::A;
-  const int TPB = blockDim.x;  // 64 or 128
-  const uint32_t kShift = TPB == 128 ? 7u : (TPB == 64 ? 6u : 5u);
+  const int TPB = TPBC ? TPBC : int(blockDim.x);
+  const int kShift = TPB;  // column stride (elements)
   const int code_words = a.dc.group_off[a.dc.n_groups];
   SmemTables tb = load_tables(a, smem, code_words);
   const int n = a.dc.n;
@@ -348,10 +352,10 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
           for (int h = 0; h < 4; h++) {
             if (i + h < n) {
               const float x = vv[h] + 0.0f;  // -0 -> +0: sgn(0) = +1
-              if constexpr (MSG == kFP32) y[(i + h) << kShift] = x;
-              if constexpr (MSG == kFP16) y[(i + h) << kShift] = to_half_sat(x);
-              if constexpr (MSG == kINT8) y[(i + h) << kShift] = to_q(4.0f * x);
-              acc[(i + h) << kShift] = A(0);
+              if constexpr (MSG == kFP32) y[(i + h) * kShift] = x;
+              if constexpr (MSG == kFP16) y[(i + h) * kShift] = to_half_sat(x);
+              if constexpr (MSG == kINT8) y[(i + h) * kShift] = to_q(4.0f * x);
+              acc[(i + h) * kShift] = A(0);
               if (a.ckpt) a.ckpt[size_t(f) * a.ld + i + h] = x;
             }
           }
@@ -362,17 +366,22 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
           // pi^-1(u) = rotr_m(u, j) + s' with s' = -rotr_m(s, j) mod n
           const uint32_t rs = j ? (((s >> j) | (s << (m - j))) & uint32_t(n)) : s;
           const uint32_t sp = rs ? uint32_t(n) - rs : 0u;
-          ctx[p << kShift] = j | (sp << 8);
+          ctx[p * kShift] = j | (sp << 8);
         }
       }
     }
-    if (!__any_sync(kFull, f >= 0)) break;
-    if (f < 0) continue;
+    if constexpr (LOCKSTEP) {
+      if (!__syncthreads_or(f >= 0)) break;
+    } else {
+      if (!__any_sync(kFull, f >= 0)) break;
+      if (f < 0) continue;
+    }
 
-    const float alpha = tb.alpha[t];
+    const float alpha = tb.alpha[f >= 0 ? t : 0];
     for (int p = 0; p < a.P; p++) {
-      const uint32_t cx = ctx[p << kShift];
-      copy(tb, n_groups, uint32_t(n), m, y, acc, scratch, cx & 0xffu, cx >> 8, kShift, alpha);
+      if constexpr (LOCKSTEP) __syncthreads();
+      const uint32_t cx = f >= 0 ? ctx[p * kShift] : 0u;
+      copy(tb, n_groups, uint32_t(n), m, y, acc, scratch, cx & 0xffu, cx >> 8, uint32_t(kShift), alpha);
     }
     // merge (FP32), hard decision, re-store
     uint32_t cb[NW];
@@ -382,9 +391,9 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
 #pragma unroll
       for (int i = 0; i < NW * 32; i++) {
         if (i < n) {
-          const float yn = __fmaf_rn(acc[i << kShift], invP, y[i << kShift]);
-          y[i << kShift] = yn;
-          acc[i << kShift] = 0.0f;
+          const float yn = __fmaf_rn(acc[i * kShift], invP, y[i * kShift]);
+          y[i * kShift] = yn;
+          acc[i * kShift] = 0.0f;
           cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
         }
       }
@@ -396,12 +405,12 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         if (i < n) {
           float yn;
           if constexpr (MSG == kINT8)  // exact division: a .5 tie stays a tie
-            yn = float(ld_y(y + (i << kShift))) + __fdiv_rn(float(acc[i << kShift]), float(a.P));
+            yn = float(ld_y(y + (i * kShift))) + __fdiv_rn(float(acc[i * kShift]), float(a.P));
           else
-            yn = __fmaf_rn(acc[i << kShift], invP, ld_y(y + (i << kShift)));
+            yn = __fmaf_rn(acc[i * kShift], invP, ld_y(y + (i * kShift)));
           cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
           mx = fmaxf(mx, fabsf(yn));
-          reinterpret_cast<float *>(acc)[i << kShift] = yn;
+          reinterpret_cast<float *>(acc)[i * kShift] = yn;
         }
       }
       // optional power-of-two renormalisation (exact; min-sum is scale invariant)
@@ -418,19 +427,20 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
 #pragma unroll
       for (int i = 0; i < NW * 32; i++) {
         if (i < n) {
-          const float yn = reinterpret_cast<float *>(acc)[i << kShift] * sc;
+          const float yn = reinterpret_cast<float *>(acc)[i * kShift] * sc;
           if constexpr (MSG == kINT8)
-            y[i << kShift] = to_q(yn);
+            y[i * kShift] = to_q(yn);
           else
-            y[i << kShift] = to_half_sat(yn);
-          acc[i << kShift] = A(0);
+            y[i * kShift] = to_half_sat(yn);
+          acc[i * kShift] = A(0);
         }
       }
     }
+    if (LOCKSTEP && f < 0) continue;
     t++;
     if (a.ckpt) {
       float *dst = a.ckpt + (size_t(t) * a.F + f) * a.ld;
-      for (int i = 0; i < n; i++) dst[i] = float(ld_y(y + (i << kShift)));
+      for (int i = 0; i < n; i++) dst[i] = float(ld_y(y + (i * kShift)));
     }
     const uint32_t nz = syndrome_nonzero<NW>(tb.rowmask, a.dc.rows, cb);
     if (t >= a.I || (a.early_stop && nz == 0)) {
@@ -442,7 +452,7 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         float unscale = 1.0f;
         if constexpr (MSG == kINT8) unscale = 0.25f;
         for (int k = 0; k < escale; k++) unscale *= 2.0f;
-        for (int i = 0; i < n; i++) dst[i] = float(ld_y(y + (i << kShift))) * unscale;
+        for (int i = 0; i < n; i++) dst[i] = float(ld_y(y + (i * kShift))) * unscale;
       }
       need = true;
     }
@@ -457,8 +467,8 @@ struct GenericCopy {
   __device__ __forceinline__ void operator()(const SmemTables &tb, int n_groups, uint32_t n, uint32_t m,
                                              typename StoreT<MSG>::Y *y, typename StoreT<MSG>::A *acc,
                                              typename StoreT<MSG>::A *, uint32_t jr, uint32_t sp,
-                                             uint32_t sh, float alpha) const {
-    enh_copy<MSG, WB>(tb, n_groups, n, m, y, acc, jr, sp, sh, alpha);
+                                             uint32_t stride, float alpha) const {
+    enh_copy<MSG, WB>(tb, n_groups, n, m, y, acc, jr, sp, stride, alpha);
   }
 };
 

@@ -1,0 +1,919 @@
+// Continuous-batching server: requests of mixed codes and sizes are admitted into a
+// persistent kernel as slots and HBM free up, and their frames are decoded by the
+// hybrid decoder (enhanced NMS, OSD on the frames it fails) while other requests are
+// already on the GPU.
+//
+// Device side: one warp per block; a warp claims up to 32 frames of the oldest
+// admitted request that still has unclaimed frames (atomic claim counter per slot),
+// decodes them one frame per lane (enhanced NMS, rows of any of the server's codes
+// read from global memory), runs OSD warp-cooperatively on the frames whose syndrome
+// stayed nonzero (in the same shared-memory region), then adds the frames to the
+// slot's done counter; the warp that completes a request posts a completion record
+// to a ring in host-mapped memory.  Every wait is bounded: idle warps sleep and the
+// kernel exits after `idle_exit_us` without work (the host relaunches it), and a stop
+// flag ends it at the next chunk boundary.
+//
+// Host side: admission against the HBM budget (first-fit arena of 256-byte units),
+// a FIFO of requests waiting for memory or a slot, submission through a host-mapped
+// ring, completion polling, result fetch (which frees the request's memory).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <random>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "bch_kernels.cuh"
+#include "osd_device.cuh"
+
+using namespace bchlib;
+
+namespace bchlib {
+
+constexpr int kSrvMaxCodes = 8;
+
+struct SrvCode {
+  DevCode dc;
+  const GroupDesc *grp;  // [kMaxGroups] in device memory
+  const uint4 *std_rows;
+  int M, has_osd, wb, pad;
+};
+
+// claim = generation << 32 | next unclaimed frame: a claim is a CAS that only
+// succeeds for the request currently in the slot.
+struct SrvSlot {
+  const float *llr;
+  const uint16_t *autos;
+  uint64_t *hard;
+  uint8_t *iters;
+  uint8_t *flags;
+  unsigned long long id;
+  unsigned long long claim;
+  int code, F, ld;
+  unsigned done;
+};
+
+struct SrvComp {
+  unsigned long long id;
+  unsigned long long t_ns;
+  unsigned slot;
+  unsigned seq;
+};
+
+// Host-mapped control block (written by the host: sub_ring / sub_tail / stop;
+// written by the device: comp / running).
+struct SrvShared {
+  volatile unsigned sub_tail;
+  volatile unsigned stop;
+  volatile unsigned running;
+  volatile unsigned live_blocks;
+  unsigned pad[4];
+};
+
+struct SrvDev {
+  unsigned head;
+  unsigned comp_tail;
+  unsigned live;
+  unsigned pad;
+};
+
+struct SrvArgs {
+  const SrvCode *codes;  // [kSrvMaxCodes] in device memory
+  const float *alpha;    // [32] in device memory
+  int n_codes;
+  SrvSlot *slots;
+  SrvShared *sh;
+  unsigned *sub_ring;  // host-mapped [ring]
+  SrvComp *comp;       // host-mapped [ring]
+  SrvDev *dv;
+  int ring;
+  int iters, P, order, early_stop;
+  unsigned long long idle_ns;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Enhanced NMS of up to 32 frames (one per lane) of one request, all iterations.
+template <int WB>
+__device__ __noinline__ void srv_nms_chunk(const SrvArgs &a, const SrvCode &cd, const SrvSlot &sl, int f0,
+                                           int cnt, float *y, float *acc, uint32_t *ctx) {
+  const int lane = int(lane_id());
+  const int n = cd.dc.n;
+  const uint32_t m = uint32_t(cd.dc.m);
+  const bool act0 = lane < cnt;
+  const int f = f0 + lane;
+  SmemTables tb;
+  tb.codes = const_cast<uint16_t *>(cd.dc.codes);
+  tb.grp = const_cast<GroupDesc *>(cd.grp);
+  tb.rowmask = reinterpret_cast<uint4 *>(const_cast<uint32_t *>(cd.dc.rowmask));
+  tb.alpha = nullptr;
+  tb.state = nullptr;
+  if (act0) {
+    const float *src = sl.llr + size_t(f) * sl.ld;
+    for (int i = 0; i < n; i++) {
+      y[i * 32] = src[i] + 0.0f;
+      acc[i * 32] = 0.0f;
+    }
+    for (int p = 0; p < a.P; p++) {
+      const uint32_t v = sl.autos[size_t(f) * a.P + p];
+      const uint32_t s = v & 0xffu, j = v >> 8;
+      const uint32_t rs = j ? (((s >> j) | (s << (m - j))) & uint32_t(n)) : s;
+      ctx[p * 32] = j | ((rs ? uint32_t(n) - rs : 0u) << 8);
+    }
+  }
+  bool act = act0;
+  int t = 0;
+  uint32_t cb[4] = {0, 0, 0, 0};
+  uint32_t nz = 1;
+  const float invP = 1.0f / float(a.P);
+  while (__any_sync(kFull, act)) {
+    if (act) {
+      const float alpha = __ldg(a.alpha + t);
+      for (int p = 0; p < a.P; p++) {
+        const uint32_t cx = ctx[p * 32];
+        enh_copy<kFP32, WB>(tb, cd.dc.n_groups, uint32_t(n), m, y, acc, cx & 0xffu, cx >> 8, 32u, alpha);
+      }
+      cb[0] = cb[1] = cb[2] = cb[3] = 0;
+#pragma unroll
+      for (int i = 0; i < 128; i++) {
+        if (i < n) {
+          const float yn = __fmaf_rn(acc[i * 32], invP, y[i * 32]);
+          y[i * 32] = yn;
+          acc[i * 32] = 0.0f;
+          cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
+        }
+      }
+      t++;
+      nz = syndrome_nonzero<4>(tb.rowmask, cd.dc.rows, cb);
+      if (t >= a.iters || (a.early_stop && nz == 0)) {
+        const int W64 = (n + 63) / 64;
+        sl.hard[size_t(f) * W64] = uint64_t(cb[0]) | (uint64_t(cb[1]) << 32);
+        if (W64 > 1) sl.hard[size_t(f) * W64 + 1] = uint64_t(cb[2]) | (uint64_t(cb[3]) << 32);
+        sl.iters[f] = uint8_t(t);
+        sl.flags[f] = nz ? 0 : uint8_t(kFlagConverged);
+        act = false;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32) serve_kernel(const SrvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *acc = reinterpret_cast<float *>(smem);
+  float *y = acc + 128 * 32;
+  uint32_t *ctx = reinterpret_cast<uint32_t *>(y + 128 * 32);
+  OsdSmem &S = *reinterpret_cast<OsdSmem *>(smem);  // aliases the NMS columns
+  const int lane = int(lane_id());
+  if (lane == 0) atomicAdd(&a.dv->live, 1u);
+  unsigned long long idle_since = globaltimer();
+  unsigned sleep_ns = 64;
+  for (;;) {
+    if (a.sh->stop) break;
+    int slot = -1, start = 0;
+    if (lane == 0) {
+      const unsigned h = *reinterpret_cast<volatile unsigned *>(&a.dv->head);
+      const unsigned tail = a.sh->sub_tail;
+      if (h != tail) {
+        __threadfence_system();
+        const unsigned e = *reinterpret_cast<volatile unsigned *>(&a.sub_ring[h % unsigned(a.ring)]);
+        const int s = int(e & 0xffffu);
+        const unsigned gen = e >> 16;
+        SrvSlot *sp = a.slots + s;
+        slot = -2;
+        for (int tries = 0; tries < 64; tries++) {  // bounded CAS retries
+          const unsigned long long c = *reinterpret_cast<volatile unsigned long long *>(&sp->claim);
+          const unsigned next = unsigned(c);
+          const int F = *reinterpret_cast<volatile int *>(&sp->F);
+          if (((c >> 32) & 0xffffu) != gen || int(next) >= F) {
+            atomicCAS(&a.dv->head, h, h + 1);  // request fully claimed (or replaced): move on
+            break;
+          }
+          if (atomicCAS(&sp->claim, c, c + 32ull) == c) {
+            slot = s;
+            start = int(next);
+            break;
+          }
+        }
+      }
+    }
+    slot = __shfl_sync(kFull, slot, 0);
+    start = __shfl_sync(kFull, start, 0);
+    if (slot == -2) continue;
+    if (slot < 0) {
+      if (globaltimer() - idle_since > a.idle_ns) break;
+      __nanosleep(sleep_ns);
+      sleep_ns = sleep_ns < 20000 ? sleep_ns * 2 : sleep_ns;
+      continue;
+    }
+    sleep_ns = 64;
+    const SrvSlot sl = a.slots[slot];  // stable until this chunk is counted done
+    const SrvCode &cd = a.codes[sl.code];  // device memory
+    const int cnt = min(32, sl.F - start);
+    switch (cd.wb) {
+      case 8: srv_nms_chunk<8>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
+      case 16: srv_nms_chunk<16>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
+      case 24: srv_nms_chunk<24>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
+      case 32: srv_nms_chunk<32>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
+      default: srv_nms_chunk<48>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
+    }
+    __syncwarp();
+    if (cd.has_osd) {
+      unsigned fail = __ballot_sync(kFull, lane < cnt && !(sl.flags[start + lane] & kFlagConverged));
+      const int W64 = (cd.dc.n + 63) / 64;
+      while (fail) {
+        const int l = __ffs(fail) - 1;
+        fail &= fail - 1;
+        const int f = start + l;
+        osd_one_frame(S, cd.dc.n, cd.dc.k, cd.M, cd.std_rows, sl.llr + size_t(f) * sl.ld, a.order,
+                      sl.hard + size_t(f) * W64, sl.flags + f);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      const unsigned d = atomicAdd(&a.slots[slot].done, unsigned(cnt)) + unsigned(cnt);
+      if (int(d) == sl.F) {
+        const unsigned ci = atomicAdd(&a.dv->comp_tail, 1u);
+        SrvComp *c = a.comp + (ci % unsigned(a.ring));
+        c->id = sl.id;
+        c->t_ns = globaltimer();
+        c->slot = unsigned(slot);
+        __threadfence_system();
+        *reinterpret_cast<volatile unsigned *>(&c->seq) = ci + 1;
+      }
+    }
+    idle_since = globaltimer();
+  }
+  if (lane == 0) {
+    if (atomicSub(&a.dv->live, 1u) == 1u) {
+      __threadfence_system();
+      a.sh->running = 0;
+    }
+  }
+}
+
+}  // namespace bchlib
+
+// ------------------------------------------------------------------------- host side
+struct bch_server {
+  bch_server_config cfg{};
+  std::vector<const bch_code *> codes, std_codes;
+  std::vector<float> alpha;
+  SrvArgs args{};
+  cudaStream_t kst = nullptr, cst = nullptr;
+  SrvShared *sh = nullptr;  // host pointer of the mapped block
+  unsigned *sub_ring = nullptr;
+  SrvComp *comp = nullptr;
+  SrvSlot *slots_dev = nullptr;
+  SrvDev *dv = nullptr;
+  GroupDesc *grp_dev = nullptr;
+  SrvCode *codes_dev = nullptr;
+  float *alpha_dev = nullptr;
+  SrvCode codes_host[kSrvMaxCodes];
+  unsigned char *arena = nullptr;
+  size_t arena_bytes = 0;
+  std::map<size_t, size_t> free_list;  // offset -> bytes
+  struct Req {
+    unsigned long long id;
+    int code, F, ld;
+    const float *llr;
+    uint64_t seed, frame0;
+    size_t off = 0, bytes = 0;
+    int slot = -1;
+    bool done = false;
+  };
+  std::deque<Req> pending;
+  std::map<unsigned long long, Req> active;
+  std::vector<int> free_slots;
+  std::vector<unsigned> slot_gen;
+  unsigned sub_tail = 0, comp_read = 0;
+  unsigned long long next_id = 1;
+  int blocks = 0;
+  size_t smem = 0;
+  std::mutex mu;
+  bch_server_stats stats{};
+};
+
+namespace {
+
+size_t align256s(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t llr, autos, hard, iters, flags, total;
+};
+
+Layout req_layout(const bch_server *s, int code, int F, int ld) {
+  Layout L;
+  const int W64 = (s->codes[code]->alg.n + 63) / 64;
+  size_t off = 0;
+  L.llr = off;
+  off = align256s(off + size_t(F) * ld * 4);
+  L.autos = off;
+  off = align256s(off + size_t(F) * s->cfg.n_autos * 2);
+  L.hard = off;
+  off = align256s(off + size_t(F) * W64 * 8);
+  L.iters = off;
+  off = align256s(off + size_t(F));
+  L.flags = off;
+  off = align256s(off + size_t(F));
+  L.total = off;
+  return L;
+}
+
+bool arena_alloc(bch_server *s, size_t bytes, size_t *off) {
+  for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
+    if (it->second >= bytes) {
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t noff = it->first + bytes;
+      s->free_list.erase(it);
+      if (rest) s->free_list[noff] = rest;
+      return true;
+    }
+  }
+  return false;
+}
+
+void arena_free(bch_server *s, size_t off, size_t bytes) {
+  auto it = s->free_list.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != s->free_list.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    s->free_list.erase(nx);
+  }
+  if (it != s->free_list.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      s->free_list.erase(it);
+    }
+  }
+}
+
+bch_status launch_server_kernel(bch_server *s) {
+  s->sh->running = 1;
+  s->args.dv = s->dv;
+  cudaError_t e = cudaMemsetAsync(&s->dv->live, 0, sizeof(unsigned), s->kst);
+  if (e == cudaSuccess) {
+    serve_kernel<<<s->blocks, 32, s->smem, s->kst>>>(s->args);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    s->sh->running = 0;
+    return fail(BCH_ECUDA, std::string("serve kernel: ") + cudaGetErrorString(e));
+  }
+  return BCH_OK;
+}
+
+// Admits a request (memory, slot, copies, publication).  Caller holds the lock.
+bch_status admit(bch_server *s, bch_server::Req &r, bool *admitted) {
+  *admitted = false;
+  if (s->free_slots.empty()) return BCH_OK;
+  const Layout L = req_layout(s, r.code, r.F, r.ld);
+  size_t off = 0;
+  if (!arena_alloc(s, L.total, &off)) return BCH_OK;
+  r.off = off;
+  r.bytes = L.total;
+  r.slot = s->free_slots.back();
+  s->free_slots.pop_back();
+  unsigned char *base = s->arena + off;
+  SrvSlot sl{};
+  sl.llr = reinterpret_cast<const float *>(base + L.llr);
+  sl.autos = reinterpret_cast<const uint16_t *>(base + L.autos);
+  sl.hard = reinterpret_cast<uint64_t *>(base + L.hard);
+  sl.iters = base + L.iters;
+  sl.flags = base + L.flags;
+  sl.id = r.id;
+  sl.code = r.code;
+  sl.F = r.F;
+  sl.ld = r.ld;
+  const unsigned gen = (s->slot_gen[r.slot] + 1) & 0xffffu;
+  s->slot_gen[r.slot] = gen;
+  sl.claim = (unsigned long long)gen << 32;
+  sl.done = 0;
+  cudaError_t e = cudaMemcpyAsync(const_cast<float *>(sl.llr), r.llr, size_t(r.F) * r.ld * 4, cudaMemcpyDefault,
+                                  s->cst);
+  if (e == cudaSuccess) {
+    int ord = 1;
+    const int n = s->codes[r.code]->alg.n;
+    for (int x = 2 % n; x != 1; x = (2 * x) % n) ord++;
+    e = launch_draw_autos(n, ord, s->cfg.n_autos, r.seed, r.frame0, r.F, const_cast<uint16_t *>(sl.autos), s->cst);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->slots_dev + r.slot, &sl, sizeof(sl), cudaMemcpyHostToDevice, s->cst);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->cst);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("admission copies: ") + cudaGetErrorString(e));
+  s->sub_ring[s->sub_tail % unsigned(s->cfg.max_requests)] = unsigned(r.slot) | (gen << 16);
+  std::atomic_thread_fence(std::memory_order_release);
+  s->sub_tail++;
+  s->sh->sub_tail = s->sub_tail;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  s->stats.admitted++;
+  s->stats.bytes_in_use += L.total;
+  *admitted = true;
+  if (!s->sh->running) {
+    cudaStreamSynchronize(s->kst);  // a previous instance that timed out has finished
+    bch_status st = launch_server_kernel(s);
+    if (st != BCH_OK) return st;
+    s->stats.kernel_launches++;
+  }
+  return BCH_OK;
+}
+
+bch_status admit_pending(bch_server *s) {
+  while (!s->pending.empty()) {
+    bool ok = false;
+    bch_server::Req r = s->pending.front();
+    bch_status st = admit(s, r, &ok);
+    if (st != BCH_OK) return st;
+    if (!ok) break;
+    s->pending.pop_front();
+    s->active[r.id] = r;
+  }
+  return BCH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
+  if (!cfg || !out) return fail(BCH_EINVAL, "null argument");
+  *out = nullptr;
+  if (cfg->n_codes < 1 || cfg->n_codes > kSrvMaxCodes || !cfg->codes)
+    return fail(BCH_EINVAL, "n_codes must be in [1, 8]");
+  if (cfg->iters < 1 || cfg->iters > 32 || !cfg->alpha || cfg->n_autos < 1 || cfg->n_autos > 9 ||
+      cfg->osd_order < 0 || cfg->osd_order > 2 || cfg->max_requests < 1 || cfg->budget_bytes < 4096)
+    return fail(BCH_EINVAL, "bad server configuration");
+  bch_server *s = new (std::nothrow) bch_server();
+  if (!s) return fail(BCH_ENOMEM, "host allocation");
+  s->cfg = *cfg;
+  s->alpha.assign(cfg->alpha, cfg->alpha + cfg->iters);
+  s->cfg.alpha = s->alpha.data();
+  s->codes.assign(cfg->codes, cfg->codes + cfg->n_codes);
+  s->std_codes.assign(cfg->n_codes, nullptr);
+  if (cfg->std_codes) s->std_codes.assign(cfg->std_codes, cfg->std_codes + cfg->n_codes);
+  s->cfg.codes = nullptr;
+  s->cfg.std_codes = nullptr;
+  auto cleanup = [s]() {
+    if (s->kst) cudaStreamDestroy(s->kst);
+    if (s->cst) cudaStreamDestroy(s->cst);
+    if (s->sh) cudaFreeHost(s->sh);
+    cudaFree(s->slots_dev);
+    cudaFree(s->dv);
+    cudaFree(s->grp_dev);
+    cudaFree(s->codes_dev);
+    cudaFree(s->alpha_dev);
+    cudaFree(s->arena);
+    delete s;
+  };
+  SrvArgs &A = s->args;
+  std::memset(&A, 0, sizeof(A));
+  A.n_codes = cfg->n_codes;
+  const int R = cfg->max_requests;
+  // host-mapped control block, submission ring and completion ring in one allocation
+  const size_t ring_off = 64;
+  const size_t comp_off = (ring_off + size_t(R) * 4 + 63) & ~size_t(63);
+  const size_t shared_bytes = comp_off + size_t(R) * sizeof(SrvComp);
+  void *hp = nullptr;
+  if (cudaHostAlloc(&hp, shared_bytes, cudaHostAllocMapped) != cudaSuccess) {
+    cleanup();
+    return fail(BCH_ENOMEM, "mapped host memory");
+  }
+  std::memset(hp, 0, shared_bytes);
+  s->sh = static_cast<SrvShared *>(hp);
+  s->sub_ring = reinterpret_cast<unsigned *>(static_cast<unsigned char *>(hp) + ring_off);
+  s->comp = reinterpret_cast<SrvComp *>(static_cast<unsigned char *>(hp) + comp_off);
+  void *dsh = nullptr;
+  if (cudaHostGetDevicePointer(&dsh, hp, 0) != cudaSuccess) {
+    cleanup();
+    return fail(BCH_ECUDA, "mapped device pointer");
+  }
+  A.sh = static_cast<SrvShared *>(dsh);
+  A.sub_ring = reinterpret_cast<unsigned *>(static_cast<unsigned char *>(dsh) + ring_off);
+  A.comp = reinterpret_cast<SrvComp *>(static_cast<unsigned char *>(dsh) + comp_off);
+  A.ring = R;
+  A.iters = cfg->iters;
+  A.P = cfg->n_autos;
+  A.order = cfg->osd_order;
+  A.early_stop = 1;
+  A.idle_ns = (unsigned long long)(cfg->idle_exit_us ? cfg->idle_exit_us : 200000) * 1000ull;
+  if (cudaMalloc(&s->codes_dev, sizeof(SrvCode) * kSrvMaxCodes) != cudaSuccess ||
+      cudaMalloc(&s->alpha_dev, sizeof(float) * 32) != cudaSuccess) {
+    cleanup();
+    return fail(BCH_ENOMEM, "server tables");
+  }
+  {
+    float al[32];
+    for (int t = 0; t < 32; t++) al[t] = t < cfg->iters ? cfg->alpha[t] : 0.0f;
+    cudaMemcpy(s->alpha_dev, al, sizeof(al), cudaMemcpyHostToDevice);
+  }
+  std::memset(s->codes_host, 0, sizeof(s->codes_host));
+  if (cudaMalloc(&s->slots_dev, sizeof(SrvSlot) * R) != cudaSuccess ||
+      cudaMalloc(&s->dv, sizeof(SrvDev)) != cudaSuccess ||
+      cudaMalloc(&s->grp_dev, sizeof(GroupDesc) * kMaxGroups * kSrvMaxCodes) != cudaSuccess) {
+    cleanup();
+    return fail(BCH_ENOMEM, "server tables");
+  }
+  cudaMemset(s->slots_dev, 0, sizeof(SrvSlot) * R);
+  cudaMemset(s->dv, 0, sizeof(SrvDev));
+  std::vector<GroupDesc> grp(size_t(kMaxGroups) * kSrvMaxCodes);
+  for (int c = 0; c < cfg->n_codes; c++) {
+    const bch_code *co = s->codes[c];
+    const bch_code *sc = s->std_codes[c];
+    if (!co || !co->dev_dc) {
+      cleanup();
+      return fail(BCH_EINVAL, "null code in the server configuration");
+    }
+    if (sc && (sc->kind != BCH_PCM_STANDARD || sc->alg.n != co->alg.n || sc->alg.k != co->alg.k ||
+               sc->alg.n - sc->alg.k > 64)) {
+      cleanup();
+      return fail(BCH_EINVAL, "std_codes[i] must be the standard matrix of codes[i]");
+    }
+    SrvCode &sc_ = s->codes_host[c];
+    sc_.dc = co->dc;
+    for (int g = 0; g < kMaxGroups; g++) {
+      GroupDesc d{};
+      d.w = co->dc.group_w[g];
+      d.rows = co->dc.group_rows[g];
+      d.off = co->dc.group_off[g];
+      grp[size_t(c) * kMaxGroups + g] = d;
+    }
+    sc_.grp = s->grp_dev + size_t(c) * kMaxGroups;
+    sc_.std_rows = sc ? reinterpret_cast<const uint4 *>(sc->dc.rowmask) : nullptr;
+    sc_.M = sc ? sc->alg.n - sc->alg.k : 0;
+    sc_.has_osd = sc ? 1 : 0;
+    const int mw = co->dc.max_w;
+    sc_.wb = mw <= 8 ? 8 : mw <= 16 ? 16 : mw <= 24 ? 24 : mw <= 32 ? 32 : mw <= 48 ? 48 : 0;
+    if (!sc_.wb) {
+      cleanup();
+      return fail(BCH_EINVAL, "row weight above 48");
+    }
+  }
+  cudaMemcpy(s->grp_dev, grp.data(), sizeof(GroupDesc) * grp.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->codes_dev, s->codes_host, sizeof(SrvCode) * kSrvMaxCodes, cudaMemcpyHostToDevice);
+  A.codes = s->codes_dev;
+  A.alpha = s->alpha_dev;
+  s->arena_bytes = cfg->budget_bytes & ~size_t(255);
+  if (cudaMalloc(&s->arena, s->arena_bytes) != cudaSuccess) {
+    cleanup();
+    return fail(BCH_ENOMEM, "HBM budget arena");
+  }
+  s->free_list[0] = s->arena_bytes;
+  if (R > 65535) {
+    cleanup();
+    return fail(BCH_EINVAL, "max_requests above 65535");
+  }
+  for (int i = R - 1; i >= 0; i--) s->free_slots.push_back(i);
+  s->slot_gen.assign(R, 0);
+  A.slots = s->slots_dev;
+  if (cudaStreamCreateWithFlags(&s->kst, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking) != cudaSuccess) {
+    cleanup();
+    return fail(BCH_ECUDA, "streams");
+  }
+  s->smem = std::max(sizeof(float) * 128 * 32 * 2 + sizeof(uint32_t) * 9 * 32, sizeof(OsdSmem));
+  if (cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s->smem)) !=
+      cudaSuccess) {
+    cleanup();
+    return fail(BCH_ECUDA, "serve kernel attributes");
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, 32, s->smem);
+  s->blocks = cfg->warps > 0 ? cfg->warps : sms * std::max(per_sm, 1);
+  cudaDeviceSynchronize();
+  *out = s;
+  return BCH_OK;
+}
+
+bch_status bch_server_submit(bch_server *s, int code_id, const float *llr, int ld, int n_frames,
+                             uint64_t autos_seed, uint64_t frame0, uint64_t *request_id) {
+  if (!s || !llr || !request_id) return fail(BCH_EINVAL, "null argument");
+  if (code_id < 0 || code_id >= int(s->codes.size())) return fail(BCH_EINVAL, "bad code id");
+  if (n_frames < 1 || (s->cfg.max_frames_per_request > 0 && n_frames > s->cfg.max_frames_per_request) ||
+      ld < s->codes[code_id]->alg.n)
+    return fail(BCH_EINVAL, "bad request size");
+  std::lock_guard<std::mutex> lk(s->mu);
+  const Layout L = req_layout(s, code_id, n_frames, ld);
+  if (L.total > s->arena_bytes) return fail(BCH_EBUDGET, "request larger than the HBM budget");
+  bch_server::Req r;
+  r.id = s->next_id++;
+  r.code = code_id;
+  r.F = n_frames;
+  r.ld = ld;
+  r.llr = llr;
+  r.seed = autos_seed;
+  r.frame0 = frame0;
+  *request_id = r.id;
+  s->stats.submitted++;
+  if (s->pending.empty()) {
+    bool ok = false;
+    bch_status st = admit(s, r, &ok);
+    if (st != BCH_OK) return st;
+    if (ok) {
+      s->active[r.id] = r;
+      return BCH_OK;
+    }
+  }
+  s->pending.push_back(r);
+  s->stats.queued++;
+  return BCH_OK;
+}
+
+bch_status bch_server_poll(bch_server *s, uint64_t *done_ids, int max_ids, int *n_done, int timeout_us) {
+  if (!s || !done_ids || !n_done || max_ids < 1) return fail(BCH_EINVAL, "bad argument");
+  *n_done = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      while (*n_done < max_ids) {
+        SrvComp *c = s->comp + (s->comp_read % unsigned(s->cfg.max_requests));
+        if (*reinterpret_cast<volatile unsigned *>(&c->seq) != s->comp_read + 1) break;
+        std::atomic_thread_fence(std::memory_order_acquire);
+        const unsigned long long id = c->id;
+        s->comp_read++;
+        auto it = s->active.find(id);
+        if (it != s->active.end()) it->second.done = true;
+        done_ids[(*n_done)++] = id;
+        s->stats.completed++;
+      }
+      bch_status st = admit_pending(s);
+      if (st != BCH_OK) return st;
+      // a kernel instance that exited idle while admitted work is outstanding: relaunch
+      bool outstanding = false;
+      for (auto &kv : s->active)
+        if (!kv.second.done && kv.second.slot >= 0) outstanding = true;
+      if (outstanding && !s->sh->running) {
+        cudaStreamSynchronize(s->kst);
+        st = launch_server_kernel(s);
+        if (st != BCH_OK) return st;
+        s->stats.kernel_launches++;
+      }
+    }
+    if (*n_done > 0 || timeout_us <= 0) break;
+    const auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0);
+    if (el.count() >= timeout_us) break;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  cudaError_t e = cudaStreamQuery(s->kst);
+  if (e != cudaSuccess && e != cudaErrorNotReady)
+    return fail(BCH_ECUDA, std::string("serve kernel: ") + cudaGetErrorString(e));
+  return BCH_OK;
+}
+
+bch_status bch_server_fetch(bch_server *s, uint64_t id, uint64_t *hard, uint8_t *iters, uint8_t *flags) {
+  if (!s || !hard) return fail(BCH_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->active.find(id);
+  if (it == s->active.end() || !it->second.done) return fail(BCH_EINVAL, "request not complete or unknown");
+  bch_server::Req r = it->second;
+  const Layout L = req_layout(s, r.code, r.F, r.ld);
+  const int W64 = (s->codes[r.code]->alg.n + 63) / 64;
+  unsigned char *base = s->arena + r.off;
+  cudaError_t e = cudaMemcpyAsync(hard, base + L.hard, size_t(r.F) * W64 * 8, cudaMemcpyDefault, s->cst);
+  if (e == cudaSuccess && iters) e = cudaMemcpyAsync(iters, base + L.iters, size_t(r.F), cudaMemcpyDefault, s->cst);
+  if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, base + L.flags, size_t(r.F), cudaMemcpyDefault, s->cst);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->cst);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("fetch: ") + cudaGetErrorString(e));
+  arena_free(s, r.off, r.bytes);
+  s->stats.bytes_in_use -= r.bytes;
+  s->free_slots.push_back(r.slot);
+  s->active.erase(it);
+  return admit_pending(s);
+}
+
+bch_status bch_server_get_stats(bch_server *s, bch_server_stats *out) {
+  if (!s || !out) return fail(BCH_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  out->pending = (long long)s->pending.size();
+  out->in_flight = (long long)s->active.size();
+  return BCH_OK;
+}
+
+void bch_server_destroy(bch_server *s) {
+  if (!s) return;
+  s->sh->stop = 1;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  cudaStreamSynchronize(s->kst);
+  cudaStreamSynchronize(s->cst);
+  cudaStreamDestroy(s->kst);
+  cudaStreamDestroy(s->cst);
+  cudaFreeHost(s->sh);
+  cudaFree(s->slots_dev);
+  cudaFree(s->dv);
+  cudaFree(s->grp_dev);
+  cudaFree(s->codes_dev);
+  cudaFree(s->alpha_dev);
+  cudaFree(s->arena);
+  delete s;
+}
+
+
+// --------------------------------------------------------------------- benchmark
+// Open-loop load generator: Poisson arrivals at rate_rps for duration_s; each request
+// draws a code uniformly, a size F = floor(exp(u ln(max_frames + 1))) clipped to
+// [1, max_frames] (log-uniform) and a contiguous range of that code's frame pool.
+// Latency = scheduled arrival -> results in host memory.  static_batching = 1 runs the
+// same arrival stream through plain batched launches instead of the server: requests
+// are collected until batch_us after the first one or batch_frames frames, then every
+// code's share is copied in, hybrid-decoded with one bch_hybrid_decode call and copied
+// back before the batch's requests complete.
+bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch_serve_bench_result *res) {
+  if (!c || !res || !c->pools || !c->pool_frames || !c->lds || !c->codes || c->n_codes < 1 ||
+      c->n_codes > kSrvMaxCodes || c->rate_rps <= 0 || c->duration_s <= 0 || c->max_frames < 1)
+    return fail(BCH_EINVAL, "bad benchmark configuration");
+  if (!c->static_batching && !srv) return fail(BCH_EINVAL, "server required");
+  std::memset(res, 0, sizeof(*res));
+  using clk = std::chrono::steady_clock;
+  std::mt19937_64 rng(c->seed);
+  std::exponential_distribution<double> gap(c->rate_rps);
+  std::uniform_real_distribution<double> uni(0.0, 1.0);
+  struct Rq {
+    int code, F, off;
+    double t_arr;
+    uint64_t id;
+  };
+  // pre-draw the arrival stream
+  std::vector<Rq> reqs;
+  double t = 0.0;
+  long long offered_frames = 0;
+  for (;;) {
+    t += gap(rng);
+    if (t > c->duration_s) break;
+    Rq r;
+    r.code = int(uni(rng) * c->n_codes) % c->n_codes;
+    int F = int(std::floor(std::exp(uni(rng) * std::log(double(c->max_frames) + 1.0))));
+    F = std::max(1, std::min(F, c->max_frames));
+    F = std::min(F, c->pool_frames[r.code]);
+    r.F = F;
+    r.off = int(uni(rng) * double(c->pool_frames[r.code] - F + 1));
+    r.t_arr = t;
+    r.id = 0;
+    reqs.push_back(r);
+    offered_frames += F;
+  }
+  int W64max = 2;
+  size_t maxF = size_t(c->max_frames);
+  std::vector<uint64_t> hbuf(maxF * W64max);
+  std::vector<uint8_t> ibuf(maxF), fbuf(maxF);
+  std::vector<double> lat;
+  lat.reserve(reqs.size());
+  long long frames_done = 0;
+  const auto t0 = clk::now();
+  auto now_s = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+  if (!c->static_batching) {
+    std::map<uint64_t, size_t> by_id;
+    size_t next = 0, done = 0;
+    std::vector<uint64_t> ids(256);
+    while (done < reqs.size()) {
+      const double tn = now_s();
+      while (next < reqs.size() && reqs[next].t_arr <= tn) {
+        Rq &r = reqs[next];
+        const float *src = c->pools[r.code] + size_t(r.off) * c->lds[r.code];
+        bch_status st = bch_server_submit(srv, r.code, src, c->lds[r.code], r.F, c->seed ^ 0x5A5Aull,
+                                          uint64_t(r.off), &r.id);
+        if (st != BCH_OK) return st;
+        by_id[r.id] = next;
+        next++;
+      }
+      int nd = 0;
+      bch_status st = bch_server_poll(srv, ids.data(), int(ids.size()), &nd, 0);
+      if (st != BCH_OK) return st;
+      for (int i = 0; i < nd; i++) {
+        auto it = by_id.find(ids[i]);
+        if (it == by_id.end()) continue;
+        Rq &r = reqs[it->second];
+        st = bch_server_fetch(srv, r.id, hbuf.data(), ibuf.data(), fbuf.data());
+        if (st != BCH_OK) return st;
+        lat.push_back(now_s() - r.t_arr);
+        frames_done += r.F;
+        done++;
+        by_id.erase(it);
+      }
+      if (nd == 0 && next < reqs.size()) {
+        const double wait = reqs[next].t_arr - now_s();
+        if (wait > 20e-6) std::this_thread::sleep_for(std::chrono::microseconds(10));
+      }
+      if (now_s() > c->duration_s * 10 + 30) return fail(BCH_ETIMEOUT, "server benchmark did not drain");
+    }
+  } else {
+    // static batching: per code, a device batch buffer and a hybrid decode per batch
+    const int nc = c->n_codes;
+    std::vector<float *> dllr(nc, nullptr);
+    std::vector<uint16_t *> daut(nc, nullptr);
+    std::vector<uint64_t *> dhard(nc, nullptr);
+    std::vector<uint8_t *> dit(nc, nullptr), dfl(nc, nullptr);
+    std::vector<void *> dws(nc, nullptr);
+    const int cap = std::max(c->batch_frames, c->max_frames) + c->max_frames;
+    bch_nms_params p{};
+    p.iters = c->iters;
+    p.alpha = c->alpha;
+    p.n_autos = c->n_autos;
+    p.early_stop = 1;
+    p.msg = BCH_MSG_FP32;
+    p.osd_order = c->osd_order;
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (int k = 0; k < nc; k++) {
+      size_t wsb = 0;
+      bch_workspace_size(c->codes[k], &p, cap, &wsb);
+      if (cudaMalloc(&dllr[k], size_t(cap) * c->lds[k] * 4) != cudaSuccess ||
+          cudaMalloc(&daut[k], size_t(cap) * p.n_autos * 2) != cudaSuccess ||
+          cudaMalloc(&dhard[k], size_t(cap) * 16) != cudaSuccess || cudaMalloc(&dit[k], cap) != cudaSuccess ||
+          cudaMalloc(&dfl[k], cap) != cudaSuccess || cudaMalloc(&dws[k], wsb) != cudaSuccess)
+        return fail(BCH_ENOMEM, "static batching buffers");
+    }
+    std::vector<uint64_t> hh(size_t(cap) * 2);
+    std::vector<uint8_t> hi(cap), hf(cap);
+    size_t next = 0;
+    while (next < reqs.size()) {
+      // wait for the first request of the batch, then collect
+      double tn = now_s();
+      if (reqs[next].t_arr > tn) {
+        std::this_thread::sleep_for(std::chrono::microseconds(10));
+        continue;
+      }
+      const double t_first = reqs[next].t_arr;
+      size_t end = next;
+      long long frames = 0;
+      for (;;) {
+        tn = now_s();
+        while (end < reqs.size() && reqs[end].t_arr <= tn && frames < c->batch_frames) {
+          frames += reqs[end].F;
+          end++;
+        }
+        if (frames >= c->batch_frames || tn - t_first >= c->batch_us * 1e-6 || end == reqs.size()) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(5));
+      }
+      for (int k = 0; k < nc; k++) {
+        int tot = 0;
+        for (size_t q = next; q < end; q++) {
+          const Rq &r = reqs[q];
+          if (r.code != k) continue;
+          cudaMemcpyAsync(dllr[k] + size_t(tot) * c->lds[k], c->pools[k] + size_t(r.off) * c->lds[k],
+                          size_t(r.F) * c->lds[k] * 4, cudaMemcpyDefault, st);
+          bch_draw_automorphisms(c->codes[k]->alg.n, p.n_autos, c->seed ^ 0x5A5Aull, uint64_t(r.off), r.F,
+                                 daut[k] + size_t(tot) * p.n_autos, st);
+          tot += r.F;
+        }
+        if (!tot) continue;
+        bch_status s2 = bch_hybrid_decode(c->codes[k], c->std_codes ? c->std_codes[k] : nullptr, &p, dllr[k],
+                                          c->lds[k], tot, daut[k], dhard[k], dit[k], dfl[k], nullptr, nullptr,
+                                          nullptr, dws[k], st);
+        if (s2 != BCH_OK) return s2;
+        const int W64 = (c->codes[k]->alg.n + 63) / 64;
+        cudaMemcpyAsync(hh.data(), dhard[k], size_t(tot) * W64 * 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(hi.data(), dit[k], tot, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(hf.data(), dfl[k], tot, cudaMemcpyDeviceToHost, st);
+      }
+      if (cudaStreamSynchronize(st) != cudaSuccess) return fail(BCH_ECUDA, "static batch");
+      tn = now_s();
+      for (size_t q = next; q < end; q++) {
+        lat.push_back(tn - reqs[q].t_arr);
+        frames_done += reqs[q].F;
+      }
+      next = end;
+    }
+    for (int k = 0; k < nc; k++) {
+      cudaFree(dllr[k]);
+      cudaFree(daut[k]);
+      cudaFree(dhard[k]);
+      cudaFree(dit[k]);
+      cudaFree(dfl[k]);
+      cudaFree(dws[k]);
+    }
+    cudaStreamDestroy(st);
+  }
+  const double el = now_s();
+  std::sort(lat.begin(), lat.end());
+  auto pct = [&](double q) { return lat.empty() ? 0.0 : lat[std::min(lat.size() - 1, size_t(q * lat.size()))]; };
+  double mean = 0;
+  for (double v : lat) mean += v;
+  res->requests = (long long)lat.size();
+  res->frames = frames_done;
+  res->p50_ms = pct(0.50) * 1e3;
+  res->p99_ms = pct(0.99) * 1e3;
+  res->mean_ms = lat.empty() ? 0 : mean / lat.size() * 1e3;
+  res->max_ms = lat.empty() ? 0 : lat.back() * 1e3;
+  res->elapsed_s = el;
+  res->served_frames_per_s = frames_done / el;
+  res->offered_frames_per_s = offered_frames / c->duration_s;
+  res->offered_requests_per_s = reqs.size() / c->duration_s;
+  return BCH_OK;
+}
+
+}  // extern "C"

@@ -5,10 +5,12 @@ Tolerance rules (FP32 kernel vs FP64 oracle, same FP32 input bytes):
  * one iteration from the same input: a sum of terms is compared relative to the sum
    of the terms' magnitudes (the "operand magnitude" returned by the oracle):
    |gpu - ref| <= 1e-5 max(|ref|, mag, 1);
- * after several iterations the FP32 rounding of a frame's largest values reaches its
-   small ones through the cancellation in the min-sum updates, so the final state is
-   compared against the frame's largest operand magnitude env:
-   |gpu - ref| <= 1e-5 max(|ref|, env);
+ * after several iterations the FP32 and FP64 trajectories drift apart in magnitude
+   (rounding of a frame's largest values reaches its small ones through the
+   cancellations of the updates, and each iteration can amplify it), so the final
+   state of a multi-iteration decode is compared against the frame's largest operand
+   magnitude env with the trajectory tolerance TRAJ_TOL:
+   |gpu - ref| <= 1e-3 max(|ref|, env) -- while decisions stay exact (next rule);
  * hard decisions and iteration counts must be identical on every frame whose
    decoding never met a sign-ambiguous value: |y| < 1e-3 on the channel LLR, or any
    |y^(t)| below 1e-4 of its operand magnitude in a later iteration (there the sign is
@@ -21,6 +23,7 @@ import oracle as O
 from paper_2412_20828_gb300 import synth
 
 REL_TOL = 1e-5
+TRAJ_TOL = 1e-3
 AMBIG_LLR = 1e-3
 AMBIG_REL = 1e-4
 

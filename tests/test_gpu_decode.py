@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import ambiguous_frames, autos_dev, frame_envelope, frames, rel_close, to_dev
+from helpers import TRAJ_TOL, ambiguous_frames, autos_dev, frame_envelope, frames, rel_close, to_dev
 from paper_2412_20828_gb300 import bchdec as B
 
 pytestmark = pytest.mark.gpu
@@ -117,7 +117,7 @@ def test_enhanced_full_decode(torch_cuda, nk, ebn0):
     assert np.array_equal(g["hard"][ok], ref["hard"][ok])
     assert np.array_equal(g["flags"][ok] & 1, ref["converged"][ok])
     env = frame_envelope(ref)[:, None]
-    err = np.abs(g["y"][:, :n] - ref["y"]) / (1e-5 * np.maximum(np.abs(ref["y"]), env))
+    err = np.abs(g["y"][:, :n] - ref["y"]) / (TRAJ_TOL * np.maximum(np.abs(ref["y"]), env))
     assert err[ok].max() <= 1.0, f"worst error {err[ok].max():.3g} x tolerance"
 
 
@@ -191,13 +191,15 @@ def test_plain_nms_standard_h(torch_cuda, ebn0):
     cw, llr = frames(n, k, F, ebn0, 500, ld=64)
     g = run_nms(torch_cuda, c, llr, None, 8, 0.78, n_autos=0)
     ref = O.nms_plain(c.dense(), llr, 8, 0.78, threads=None)
-    amb = np.any(np.abs(llr[:, :n]) < 1e-3, axis=1) | (ref["margin_rel"] < 1e-4)
+    # a sign is decided by rounding when a value is within a few FP32 ulps (times the
+    # iterations) of zero relative to its own operands: 2e-5 leaves a 4x margin
+    amb = np.any(np.abs(llr[:, :n]) < 1e-3, axis=1) | (ref["margin_rel"] < 2e-5)
     assert amb.mean() < 0.1
     ok = ~amb
     assert np.array_equal(g["iters"][ok], ref["iters"][ok])
     assert np.array_equal(g["hard"][ok], ref["hard"][ok])
     env = ref["env"][:, None]
-    err = np.abs(g["y"][:, :n] - ref["y"]) / (1e-5 * np.maximum(np.abs(ref["y"]), env))
+    err = np.abs(g["y"][:, :n] - ref["y"]) / (TRAJ_TOL * np.maximum(np.abs(ref["y"]), env))
     assert err[ok].max() <= 1.0, f"worst error {err[ok].max():.3g} x tolerance"
     # one iteration from the same input: element-wise against the operand magnitude
     g1 = run_nms(torch_cuda, c, llr, None, 1, 0.78, n_autos=0, early_stop=False)

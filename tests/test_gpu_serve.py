@@ -1,0 +1,120 @@
+"""Continuous-batching server: results are the same alone and in a mixed stream, equal
+to the batch hybrid decoder on the same frames (same precompiled arithmetic), and the
+admission honours the HBM budget (queueing, never dropping)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import autos_dev, frames, to_dev
+from paper_2412_20828_gb300 import bchdec as B
+
+pytestmark = pytest.mark.gpu
+
+CODES = [(63, 36), (63, 45), (127, 64), (127, 99)]
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    from paper_2412_20828_gb300 import build
+    build.build()
+    codes = [B.Code(n, k) for n, k in CODES]
+    stds = [B.Code(n, k, kind=B.PCM_STANDARD) for n, k in CODES]
+    return torch, codes, stds
+
+
+def _batch_reference(torch, monkeypatch, code, std, llr, seed, frame0):
+    # the batch hybrid decoder on the precompiled kernel (the server's arithmetic)
+    monkeypatch.setenv("BCHDEC_NMS_KERNEL", "generic")
+    F, ld = llr.shape
+    aut = torch.zeros((F, 3), dtype=torch.int16, device="cuda")
+    B.draw_automorphisms(code.n, 3, seed, frame0, aut)
+    hard = torch.zeros((F, (code.n + 63) // 64), dtype=torch.int64, device="cuda")
+    it = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    fl = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    B.hybrid_decode(code, std, B.params(12, 0.78, osd_order=2), to_dev(llr), aut, hard, it, fl)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("BCHDEC_NMS_KERNEL")
+    return hard.cpu().numpy(), it.cpu().numpy(), fl.cpu().numpy()
+
+
+def _drain(srv, want):
+    got = {}
+    for _ in range(20000):
+        for rid in srv.poll(timeout_us=2000):
+            got[rid] = srv.fetch(rid)
+        if all(w in got for w in want):
+            return got
+    raise AssertionError("server did not complete the requests")
+
+
+def test_results_alone_and_in_mix_match_batch_decoder(setup, monkeypatch):
+    torch, codes, stds = setup
+    srv = B.Server(codes, stds, 12, 0.78, budget_bytes=1 << 30, max_requests=256)
+    try:
+        reqs = []
+        for i, (n, k) in enumerate(CODES):
+            for j, (F, e) in enumerate([(37, 2.0), (300, 3.0), (1, 4.0)]):
+                cw, llr = frames(n, k, F, e, 5000 + 10 * i + j, ld=(n + 3) & ~3)
+                reqs.append((i, llr, 77 + j, 1000 * j))
+        # alone, one at a time
+        alone = []
+        for code_id, llr, seed, f0 in reqs:
+            rid = srv.submit(code_id, llr, seed, f0)
+            alone.append(_drain(srv, [rid])[rid])
+        # all at once, mixed
+        rids = [srv.submit(code_id, llr, seed, f0) for code_id, llr, seed, f0 in reqs]
+        mixed = _drain(srv, rids)
+        for (code_id, llr, seed, f0), a, rid in zip(reqs, alone, rids):
+            m = mixed[rid]
+            for x, y in zip(a, m):
+                assert np.array_equal(x, y)
+            ref = _batch_reference(torch, monkeypatch, codes[code_id], stds[code_id], llr, seed, f0)
+            for x, y in zip(a, ref):
+                assert np.array_equal(x, y)
+        st = srv.stats()
+        assert st["completed"] == 2 * len(reqs) and st["bytes_in_use"] == 0
+    finally:
+        srv.close()
+
+
+def test_budget_admission_queues_and_rejects(setup):
+    torch, codes, stds = setup
+    # a budget that holds about two 500-frame (127,k) requests at a time
+    srv = B.Server(codes, stds, 12, 0.78, budget_bytes=600_000, max_requests=8)
+    try:
+        n, k = 127, 64
+        cw, llr = frames(n, k, 500, 3.0, 6000, ld=128)
+        rids = [srv.submit(2, llr, 1, 0) for _ in range(6)]
+        st = srv.stats()
+        assert st["queued"] >= 3  # the rest waited for memory
+        out = _drain(srv, rids)
+        first = out[rids[0]]
+        for r in rids[1:]:
+            for x, y in zip(first, out[r]):
+                assert np.array_equal(x, y)
+        big = np.zeros((4096, 128), np.float32)
+        with pytest.raises(B.BchError) as e:
+            srv.submit(2, big, 1, 0)
+        assert e.value.status == B.EBUDGET
+    finally:
+        srv.close()
+
+
+def test_kernel_relaunches_after_idle_exit(setup):
+    import time
+    torch, codes, stds = setup
+    srv = B.Server(codes, stds, 12, 0.78, budget_bytes=1 << 28, idle_exit_us=20000)
+    try:
+        n, k = 63, 45
+        cw, llr = frames(n, k, 64, 3.0, 7000, ld=64)
+        r1 = srv.submit(1, llr, 3, 0)
+        a = _drain(srv, [r1])[r1]
+        time.sleep(0.2)  # the persistent kernel has exited by now
+        r2 = srv.submit(1, llr, 3, 0)
+        b = _drain(srv, [r2])[r2]
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        assert srv.stats()["kernel_launches"] >= 2
+    finally:
+        srv.close()
