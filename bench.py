@@ -211,9 +211,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     args = ap.parse_args()
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2412_20828_gb300 import dist as D
+    rank, world, local = D.env_ranks()
 
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -246,7 +245,7 @@ def main():
         p = B.params(ITERS, ALPHA, n_autos=P_AUTOS, early_stop=True, msg=msg, osd_order=OSD_ORDER)
         llr = torch.empty((F, ld), dtype=torch.float32, device=dev)
         cw = torch.empty((F, 1), dtype=torch.int64, device=dev)
-        base = rank * 1_000_000_000
+        base = D.frame_base(rank)
         for pi, e in enumerate(POINTS):
             B.gen_frames(code, e, e, SEED_FRAMES, base + pi * 10_000_000, llr[pi * Bp:(pi + 1) * Bp],
                          cw[pi * Bp:(pi + 1) * Bp])
@@ -309,10 +308,9 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    if dist:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = D.max_over_ranks(elapsed, device=dev)
+    for st in states:
+        D.sum_over_ranks(st["ctr"])
 
     # ---- counters, edge updates, roofline of the NMS kernel
     per_point = []
@@ -333,7 +331,7 @@ def main():
             edge_updates += int(c[5]) * P_AUTOS * E
     frames_per_step = F * len(CODES)
     ms = elapsed / args.steps * 1e3
-    value = frames_per_step * world / (elapsed / args.steps)
+    value = D.job_throughput(frames_per_step, world, elapsed / args.steps)
     eups = edge_updates / nms_time
     peaks = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count

@@ -104,6 +104,16 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
+__device__ __forceinline__ SrvSlot load_slot(const SrvSlot *p) {
+  SrvSlot s;
+  static_assert(sizeof(SrvSlot) % 8 == 0, "slot layout");
+  const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p);
+  unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s);
+#pragma unroll
+  for (int i = 0; i < int(sizeof(SrvSlot) / 8); i++) dst[i] = __ldcg(src + i);
+  return s;
+}
+
 // Enhanced NMS of up to 32 frames (one per lane) of one request, all iterations.
 template <int WB>
 __device__ __noinline__ void srv_nms_chunk(const SrvArgs &a, const SrvCode &cd, const SrvSlot &sl, int f0,
@@ -217,7 +227,8 @@ __global__ void __launch_bounds__(32) serve_kernel(const SrvArgs a) {
       continue;
     }
     sleep_ns = 64;
-    const SrvSlot sl = a.slots[slot];  // stable until this chunk is counted done
+    // the host rewrites a slot between requests: read the descriptor past L1
+    const SrvSlot sl = load_slot(a.slots + slot);  // stable until this chunk is counted done
     const SrvCode &cd = a.codes[sl.code];  // device memory
     const int cnt = min(32, sl.F - start);
     switch (cd.wb) {
