@@ -309,7 +309,8 @@ def main():
     clocks = sampler.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     elapsed = D.max_over_ranks(elapsed, device=dev)
-    for st in states:
+    for st in states:  # this rank's counters feed its own kernel's roofline
+        st["ctr_local"] = st["ctr"].cpu().numpy().copy()
         D.sum_over_ranks(st["ctr"])
 
     # ---- counters, edge updates, roofline of the NMS kernel
@@ -328,7 +329,7 @@ def main():
                               "fer": c[1] / c[0], "ber": c[2] / (c[0] * st["n"]),
                               "osd_frames": int(c[4]), "nms_fer": 1 - c[6] / c[0],
                               "avg_iters": c[5] / c[0], "undetected": int(c[3])})
-            edge_updates += int(c[5]) * P_AUTOS * E
+            edge_updates += int(st["ctr_local"][pi][5]) * P_AUTOS * E
     frames_per_step = F * len(CODES)
     ms = elapsed / args.steps * 1e3
     value = D.job_throughput(frames_per_step, world, elapsed / args.steps)
