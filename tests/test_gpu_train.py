@@ -75,3 +75,58 @@ def test_train_alpha_reduces_loss(torch_cuda):
                                 ebn0_hi=5.0, seed=3, lr=0.02)
     assert np.all(np.isfinite(alpha)) and np.all(np.isfinite(hist))
     assert hist[-5:].mean() < hist[:5].mean()
+
+
+def test_autograd_function_matches_oracle_gradient(torch_cuda):
+    """The torch.autograd front end gives the oracle's dLoss/dalpha and dLoss/dllr."""
+    torch = torch_cuda
+    from paper_2412_20828_gb300 import autograd as AG
+    n, k = 63, 45
+    c = B.Code(n, k)
+    Ho = c.dense()
+    I = 5
+    alpha0 = np.array([0.6, 0.7, 0.75, 0.8, 0.85])
+    cw, llr = frames(n, k, 256, 2.5, 913, ld=64)
+    autos = O.draw_autos(n, 3, 17, 0, 256)
+    _, _, _, _, tm = O.train_grad(Ho, llr, autos, I, alpha0, cw, return_margin=True)
+    tr0 = O.nms_enhanced(Ho, llr, autos, I, alpha0, early_stop=False, trace=True)
+    sel = np.nonzero((tm > 1e-4) & ~ambiguous_frames(llr, tr0, n))[0][:96]
+    assert sel.size >= 48
+    cw, llr, autos = cw[sel], np.ascontiguousarray(llr[sel]), np.ascontiguousarray(autos[sel])
+    loss_ref, da_ref, dl_ref, _ = O.train_grad(Ho, llr, autos, I, alpha0, cw)
+    x = to_dev(llr).requires_grad_(True)
+    alpha = torch.tensor(alpha0, dtype=torch.float32, device="cuda", requires_grad=True)
+    y = AG.enhanced_nms(x, alpha, c, autos_dev(autos))
+    loss = AG.bce(y, to_dev(B.pack_bits(cw)), c)
+    loss.backward()
+    assert float(loss) == pytest.approx(loss_ref, rel=1e-4)
+    assert np.allclose(alpha.grad.cpu().numpy(), da_ref, rtol=2e-3,
+                       atol=1e-6 * np.abs(da_ref).max())
+    g = x.grad.cpu().numpy()[:, :n]
+    scale = np.abs(dl_ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(g - dl_ref) <= 1e-3 * scale + 1e-12)
+
+
+def test_autograd_training_loop_on_simulated_frames(torch_cuda):
+    """alpha_t trained by torch.optim through the backward kernel on frames the decoder
+    simulates itself (Eb/N0 uniform in [2, 5] dB): the loss falls."""
+    torch = torch_cuda
+    from paper_2412_20828_gb300 import autograd as AG
+    c = B.Code(63, 36)
+    I, F = 6, 8192
+    alpha = AG.alpha_init(I, 0.5)
+    opt = torch.optim.Adam([alpha], lr=0.02)
+    llr = torch.empty((F, 64), dtype=torch.float32, device="cuda")
+    cw = torch.empty((F, 1), dtype=torch.int64, device="cuda")
+    aut = torch.empty((F, 3), dtype=torch.int16, device="cuda")
+    hist = []
+    for step in range(25):
+        B.gen_frames(c, 2.0, 5.0, 77, step * F, llr, cw)
+        B.draw_automorphisms(63, 3, 78, step * F, aut)
+        opt.zero_grad()
+        loss = AG.bce(AG.enhanced_nms(llr, alpha, c, aut), cw, c)
+        loss.backward()
+        opt.step()
+        hist.append(float(loss))
+    assert np.all(np.isfinite(hist)) and torch.isfinite(alpha).all()
+    assert np.mean(hist[-5:]) < np.mean(hist[:5])
