@@ -194,6 +194,26 @@ def run_serving(B, torch, dev, seconds, rate):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def run_training(B, torch, steps, batch=65536, iters=12):
+    """BCH(127,64) enhanced NMS (P = 3), alpha_1..alpha_12 trained from 0.78 by Adam on
+    batches of 65 536 frames at Eb/N0 uniform in [2, 5] dB that the library simulates,
+    BCE loss on the final LLRs.  One step = frame generation, checkpointed forward,
+    loss, backward kernel and the update."""
+    code = B.Code(127, 64)
+    B.train_alpha(code, 3, iters, 0.78, 2, batch, 2.0, 5.0, 11, 0.01)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    alpha, hist = B.train_alpha(code, 3, iters, 0.78, steps, batch, 2.0, 5.0, 12, 0.01)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    code.close()
+    return {"workload": "BCH(127,64) H_o, P=3, 12 iterations, batch 65536, Eb/N0 U[2,5] dB, "
+                        "Adam lr 0.01 from alpha=0.78",
+            "steps": steps, "ms_per_step": dt / steps * 1e3, "frames_per_s": steps * batch / dt,
+            "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+            "alpha": [round(float(a), 4) for a in alpha]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,6 +229,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="duration of the serving stream (0 skips serving)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--train-steps", type=int, default=20,
+                    help="Adam steps of the BCH(127,64) alpha_t training leg (0 skips it)")
     args = ap.parse_args()
 
     from paper_2412_20828_gb300 import dist as D
@@ -382,6 +404,11 @@ def main():
     if rank == 0 and args.serve_seconds > 0:
         serving = run_serving(B, torch, dev, args.serve_seconds, args.serve_rate)
 
+    # ---- training: per-iteration alpha_t of BCH(127,64) through the backward kernel
+    training = None
+    if rank == 0 and args.train_steps > 0:
+        training = run_training(B, torch, args.train_steps)
+
     # ---- CPU baseline: the oracle on a bounded sample, and FER agreement
     cpu = None
     fer_match = None
@@ -415,7 +442,7 @@ def main():
                        "parallelism": f"frames sharded over {world} GPU(s)"},
             "edge_updates_per_s": eups, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": args.steps * len(CODES) * (NPT + 1 + 2 + 1 + NPT),
-            "serving": serving,
+            "serving": serving, "training": training,
             "fer_match_oracle_ci95": fer_match, "per_point": per_point,
         }
         print(json.dumps(line), flush=True)

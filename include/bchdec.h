@@ -118,6 +118,16 @@ bch_status bch_build_pcm_host(int n, int k, bch_pcm_kind kind, int m_rows, uint6
 bch_status bch_nms_kernel_info(const bch_code *code, int msg, int n_autos, char *buf,
                                size_t capacity);
 
+/* Compiles the run-time specialised enhanced-NMS kernel for the optimized matrix that
+ * bch_build_pcm(n, k, BCH_PCM_OPTIMIZED, m_rows, seed, opts) builds, for sm_103a with
+ * NVRTC and ptxas reporting on, without loading it: no GPU is needed.  log
+ * (caller-owned, capacity bytes, always NUL-terminated) receives the compiler output
+ * -- registers, spills, shared memory -- or the errors.  BCH_ECUDA when the compile
+ * fails or NVRTC is missing; the matrix builder's errors as bch_build_pcm.  No
+ * counterpart in the paper: a build and tuning aid for the specialised kernel. */
+bch_status bch_nms_jit_check(int n, int k, int m_rows, uint64_t seed, const bch_pcm_opts *opts,
+                             int msg, char *log, size_t capacity);
+
 /* Dimensions of a code object: n, k, rows, edges (ones in the matrix), max row weight. */
 bch_status bch_code_info(const bch_code *code, int *n, int *k, int *rows, int *edges,
                          int *max_row_weight);

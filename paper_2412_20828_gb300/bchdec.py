@@ -23,7 +23,7 @@ FLAG_CONVERGED, FLAG_OSD = 1, 2
 
 # Every symbol the header declares (checked by the tests without a GPU).
 EXPORTS = (
-    "bch_build_pcm", "bch_build_pcm_host", "bch_nms_kernel_info", "bch_code_info", "bch_pcm_export", "bch_code_free",
+    "bch_build_pcm", "bch_build_pcm_host", "bch_nms_kernel_info", "bch_nms_jit_check", "bch_code_info", "bch_pcm_export", "bch_code_free",
     "bch_draw_automorphisms", "bch_draw_automorphisms_host", "bch_gen_frames",
     "bch_workspace_size", "bch_nms_decode", "bch_hybrid_decode", "bch_hybrid_decode_noalloc",
     "bch_osd_decode",
@@ -105,6 +105,7 @@ def load():
             "bch_build_pcm": (st, [i, i, i, i, u64, C.POINTER(PcmOpts), C.POINTER(P)]),
             "bch_build_pcm_host": (st, [i, i, i, i, u64, C.POINTER(PcmOpts), P, sz, C.POINTER(i)]),
             "bch_nms_kernel_info": (st, [P, i, i, C.c_char_p, sz]),
+            "bch_nms_jit_check": (st, [i, i, i, u64, P, i, C.c_char_p, sz]),
             "bch_code_info": (st, [P, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i),
                                    C.POINTER(i)]),
             "bch_pcm_export": (st, [P, P, sz]),
@@ -237,6 +238,18 @@ def build_pcm_host(n, k, kind=PCM_OPTIMIZED, m_rows=0, seed=0x2412_20828, q_roun
     _check(load().bch_build_pcm_host(n, k, kind, m_rows, seed, C.byref(opts), _ptr(out), out.nbytes,
                                      C.byref(rows)), "bch_build_pcm_host")
     return np.ascontiguousarray(out[: rows.value])
+
+
+def nms_jit_check(n, k, msg=MSG_FP32, m_rows=0, seed=0x2412_20828) -> str:
+    """Compiles the specialised kernel of the optimized matrix of BCH(n, k) (no GPU
+    needed); returns the compiler report (registers, spills) or raises BchError with
+    the compile errors."""
+    buf = C.create_string_buffer(1 << 16)
+    rc = load().bch_nms_jit_check(n, k, m_rows, seed, None, msg, buf, 1 << 16)
+    if rc != OK:
+        raise BchError(rc, "bch_nms_jit_check",
+                       buf.value.decode(errors="replace") or load().bch_last_error().decode())
+    return buf.value.decode(errors="replace")
 
 
 def params(iters, alpha, n_autos=3, early_stop=True, msg=MSG_FP32, rescale=False, osd_order=2):

@@ -15,6 +15,7 @@ using namespace bchlib;
 
 namespace bchlib {
 cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err);
+bool jit_compile_check(const bch_code *c, int msg, std::string *log);
 int jit_block_size(int n);
 int jit_scratch_words(int n);
 size_t nms_table_bytes_host(const DevCode &dc);
@@ -315,6 +316,19 @@ bch_status bch_nms_kernel_info(const bch_code *code, int msg, int n_autos, char 
   }
   std::snprintf(buf, capacity, "%s", info.c_str());
   return BCH_OK;
+}
+
+bch_status bch_nms_jit_check(int n, int k, int m_rows, uint64_t seed, const bch_pcm_opts *opts, int msg,
+                             char *log, size_t capacity) {
+  if (!log || capacity == 0 || msg < BCH_MSG_FP32 || msg > BCH_MSG_INT8) return fail(BCH_EINVAL, "bad argument");
+  log[0] = '\0';
+  bch_code c;
+  bch_status s = build_host(n, k, BCH_PCM_OPTIMIZED, m_rows, seed, opts, &c);
+  if (s != BCH_OK) return s;
+  std::string text;
+  const bool ok = jit_compile_check(&c, msg, &text);
+  std::snprintf(log, capacity, "%s", text.c_str());
+  return ok ? BCH_OK : fail(BCH_ECUDA, "NVRTC compile failed");
 }
 
 bch_status bch_code_info(const bch_code *c, int *n, int *k, int *rows, int *edges, int *max_w) {

@@ -15,6 +15,7 @@
 #include <dlfcn.h>
 #include <nvrtc.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -78,13 +79,19 @@ NvrtcApi &nvrtc() {
 // row's negative entries, taken from the copy's sign mask with the row mask as an
 // immediate.  m_j(u) is min1 except at the row's minimum, handled by a predicated add
 // of (v2 - v1) -- this keeps min/max/compare work on the ALU pipe down to ~4 operations
-// per edge and moves the additions to the FMA pipe.
+// per edge and moves the additions to the FMA pipe.  The two smallest magnitudes are
+// tracked two edges at a time: with lo/hi the sorted pair, min1' = min(min1, lo) and
+// min2' = min(max(min1, lo), min2, hi) (second smallest of four values with
+// min1 <= min2), 5 operations per pair with a three-input minimum instead of 6.
 const char *row_macros(int msg) {
   if (msg == 2)
     return R"(
 #define BCH_VT int
 #define BCH_R0 { int m1_ = 1 << 20, m2_ = 1 << 20, a_;
 #define BCH_R1(u) a_ = abs(z[u]); m2_ = min(m2_, max(m1_, a_)); m1_ = min(m1_, a_);
+#define BCH_R1F(u, v) { const int p_ = abs(z[u]), q_ = abs(z[v]); m1_ = min(p_, q_); m2_ = max(p_, q_); }
+#define BCH_R1P(u, v) { const int p_ = abs(z[u]), q_ = abs(z[v]); const int lo_ = min(p_, q_); \
+  m2_ = __vimin3_s32(m2_, max(m1_, lo_), max(p_, q_)); m1_ = min(m1_, lo_); }
 #define BCH_RM(SG) const int c1_ = __double2int_rn(double(alpha) * double(m1_)); \
   const int c2_ = __double2int_rn(double(alpha) * double(m2_)); \
   const bool neg_ = (SG); const int v1_ = neg_ ? -c1_ : c1_; const int dv_ = (neg_ ? -c2_ : c2_) - v1_;
@@ -97,6 +104,10 @@ const char *row_macros(int msg) {
 #define BCH_VT float
 #define BCH_R0 { float m1_ = FLT_MAX, m2_ = FLT_MAX;
 #define BCH_R1(u) m2_ = fminf(m2_, fmaxf(m1_, fabsf(z[u]))); m1_ = fminf(m1_, fabsf(z[u]));
+#define BCH_R1F(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); \
+  m1_ = fminf(a_, b_); m2_ = fmaxf(a_, b_); }
+#define BCH_R1P(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); const float lo_ = fminf(a_, b_); \
+  m2_ = bch_min3f(m2_, fmaxf(m1_, lo_), fmaxf(a_, b_)); m1_ = fminf(m1_, lo_); }
 #define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
   const float v1_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m1_))), sg_); \
   const float dv_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m2_))), sg_) - v1_;
@@ -108,6 +119,10 @@ const char *row_macros(int msg) {
 #define BCH_VT float
 #define BCH_R0 { float m1_ = FLT_MAX, m2_ = FLT_MAX;
 #define BCH_R1(u) m2_ = fminf(m2_, fmaxf(m1_, fabsf(z[u]))); m1_ = fminf(m1_, fabsf(z[u]));
+#define BCH_R1F(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); \
+  m1_ = fminf(a_, b_); m2_ = fmaxf(a_, b_); }
+#define BCH_R1P(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); const float lo_ = fminf(a_, b_); \
+  m2_ = bch_min3f(m2_, fmaxf(m1_, lo_), fmaxf(a_, b_)); m1_ = fminf(m1_, lo_); }
 #define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
   const float v1_ = flip_sign(alpha * m1_, sg_); const float dv_ = flip_sign(alpha * m2_, sg_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
@@ -127,14 +142,34 @@ std::map<std::string, std::shared_ptr<Compiled>> g_cache;
 
 }  // namespace
 
-int jit_block_size(int n) { return n <= 63 ? 384 : 64; }
+namespace {
+int env_int(const char *name, int lo, int hi, int dflt) {
+  const char *v = std::getenv(name);
+  if (!v) return dflt;
+  const int x = std::atoi(v);
+  return x >= lo && x <= hi ? x : dflt;
+}
+}  // namespace
+
+// Threads per block: 384 for n <= 63 (three warps per scheduler, all in lockstep so the
+// straight-line body is fetched once per block), 64 for n = 127.  BCHDEC_JIT_TPB
+// (a multiple of 32, 64..512) overrides it for n <= 63 -- a tuning knob.
+int jit_block_size(int n) {
+  if (n > 63) return 64;
+  const int t = env_int("BCHDEC_JIT_TPB", 64, 512, 384);
+  return t % 32 == 0 ? t : 384;
+}
+// BCHDEC_JIT_PAIRS=0 tracks min1/min2 one edge at a time (tuning knob; default pairs).
+bool jit_pairs() { return env_int("BCHDEC_JIT_PAIRS", 0, 1, 1) == 1; }
 bool jit_lockstep(int n) { return n <= 63; }
-// Resident blocks per SM the register budget is sized for (3 x 128 threads for n <= 63:
-// at most 170 registers, enough for the 2n register-resident values plus temporaries).
+// Resident blocks per SM the register budget is sized for: 384 threads per SM for
+// n <= 63 (at most 170 registers each, about the 2n register-resident values plus
+// temporaries; a block of 256 gets 255).
 int jit_min_blocks(int n) {
   const char *v = std::getenv("BCHDEC_JIT_MIN_BLOCKS");  // tuning knob (register budget)
   if (v && std::atoi(v) >= 1 && std::atoi(v) <= 8) return std::atoi(v);
-  return n <= 63 ? 1 : 2;
+  if (n <= 63) return std::max(1, 384 / jit_block_size(n));
+  return 2;
 }
 int jit_scratch_words(int n) { return n <= 63 ? 0 : n; }
 
@@ -149,7 +184,11 @@ std::string jit_source(const bch_code *c, int msg) {
        "typedef unsigned long long uint64_t;\ntypedef unsigned long long uintptr_t;\n"
        "#define FLT_MAX 3.402823466e+38f\n#include <cuda_fp16.h>\n";
   o << kDevTypesText << "\n" << kNmsDeviceText << "\n";
-  o << "namespace bchlib {\n" << row_macros(msg);
+  o << "namespace bchlib {\n"
+    << "__device__ __forceinline__ float bch_min3f(float a, float b, float c) {\n"
+    << "  float d;\n  asm(\"min.f32 %0, %1, %2, %3;\" : \"=f\"(d) : \"f\"(a), \"f\"(b), \"f\"(c));\n"
+    << "  return d;\n}\n"
+    << row_macros(msg);
   if (scratch)
     o << "#define BCH_SV(u) scr[(u) * " << tpb << "]\n";
   else
@@ -189,7 +228,14 @@ std::string jit_source(const bch_code *c, int msg) {
     }
     sg << ") & 1u)";
     o << "    BCH_R0";
-    for (int u : cols) o << " BCH_R1(" << u << ")";
+    size_t e = 0;
+    const bool pairs = jit_pairs();
+    if (pairs && cols.size() >= 2) {
+      o << " BCH_R1F(" << cols[0] << ", " << cols[1] << ")";
+      e = 2;
+    }
+    for (; pairs && e + 1 < cols.size(); e += 2) o << " BCH_R1P(" << cols[e] << ", " << cols[e + 1] << ")";
+    for (; e < cols.size(); e++) o << " BCH_R1(" << cols[e] << ")";
     o << " BCH_RM(" << sg.str() << ")";
     for (int u : cols) o << " BCH_R2(" << u << ")";
     o << " BCH_RE\n";
@@ -259,6 +305,33 @@ cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
   }
   if (!cp->kernel) *err = cp->err;
   return cp->kernel;
+}
+
+// Compiles the specialised source with ptxas reporting on; no GPU is needed.  Returns
+// false with *log holding the compiler output on failure.
+bool jit_compile_check(const bch_code *c, int msg, std::string *log) {
+  NvrtcApi &api = nvrtc();
+  if (!api.ok) {
+    *log = api.err;
+    return false;
+  }
+  const std::string src = jit_source(c, msg);
+  nvrtcProgram prog = nullptr;
+  if (api.create(&prog, src.c_str(), "bch_nms_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    *log = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-I/usr/local/cuda/include",
+                        "-lineinfo", "--ptxas-options=-v"};
+  const nvrtcResult r = api.compile(prog, 5, opts);
+  size_t ls = 0;
+  api.log_size(prog, &ls);
+  std::string text(ls, '\0');
+  if (ls) api.log(prog, &text[0]);
+  while (!text.empty() && text.back() == '\0') text.pop_back();
+  api.destroy(&prog);
+  *log = text;
+  return r == NVRTC_SUCCESS;
 }
 
 }  // namespace bchlib

@@ -9,24 +9,10 @@ __global__ void draw_autos_kernel(int n, int ord, int P, uint64_t seed, uint64_t
                                   uint16_t *out) {
   const int fi = blockIdx.x * blockDim.x + threadIdx.x;
   if (fi >= F) return;
-  const uint64_t f = frame0 + uint64_t(fi);
+  uint32_t v[9];
+  draw_frame_autos(n, ord, P, seed, frame0 + uint64_t(fi), v);
   uint16_t *o = out + size_t(fi) * P;
-  uint32_t prev[9];
-  for (int p = 0; p < P; p++) {
-    uint32_t s = 0, j = 0;
-    for (int att = 0; att < 16; att++) {
-      const uint64_t cnt = 1 + (f * uint64_t(P) + uint64_t(p)) * 16 + uint64_t(att);
-      const uint64_t x = splitmix64_mix_d(seed + 0x9E3779B97F4A7C15ULL * cnt);
-      s = uint32_t(((x & 0xffffffffULL) * uint64_t(n)) >> 32);
-      j = uint32_t(((x >> 32) * uint64_t(ord)) >> 32);
-      bool clash = false;
-      for (int q = 0; q < p; q++)
-        if (prev[q] == (s | (j << 8))) clash = true;
-      if (!clash) break;
-    }
-    prev[p] = s | (j << 8);
-    o[p] = uint16_t(prev[p]);
-  }
+  for (int p = 0; p < P; p++) o[p] = uint16_t(v[p]);
 }
 
 cudaError_t launch_draw_autos(int n, int ord, int P, uint64_t seed, uint64_t frame0, int F,

@@ -13,6 +13,10 @@
 // kernel exits after `idle_exit_us` without work (the host relaunches it), and a stop
 // flag ends it at the next chunk boundary.
 //
+// The automorphisms of a frame are drawn inside the kernel from (seed, frame index):
+// admission launches no kernel, because the persistent kernel holds every SM's shared
+// memory and a second kernel would not be scheduled until it exits.
+//
 // Host side: admission against the HBM budget (first-fit arena of 256-byte units),
 // a FIFO of requests waiting for memory or a slot, submission through a host-mapped
 // ring, completion polling, result fetch (which frees the request's memory).
@@ -43,14 +47,14 @@ struct SrvCode {
   DevCode dc;
   const GroupDesc *grp;  // [kMaxGroups] in device memory
   const uint4 *std_rows;
-  int M, has_osd, wb, pad;
+  int M, has_osd, wb, ord;  // ord: order of 2 mod n (Frobenius exponents)
 };
 
 // claim = generation << 32 | next unclaimed frame: a claim is a CAS that only
 // succeeds for the request currently in the slot.
 struct SrvSlot {
   const float *llr;
-  const uint16_t *autos;
+  unsigned long long seed, frame0;  // automorphisms of frame f: draw (seed, frame0 + f)
   uint64_t *hard;
   uint8_t *iters;
   uint8_t *flags;
@@ -135,8 +139,10 @@ __device__ __noinline__ void srv_nms_chunk(const SrvArgs &a, const SrvCode &cd, 
       y[i * 32] = src[i] + 0.0f;
       acc[i * 32] = 0.0f;
     }
+    uint32_t va[9];
+    draw_frame_autos(n, cd.ord, a.P, sl.seed, sl.frame0 + uint64_t(f), va);
     for (int p = 0; p < a.P; p++) {
-      const uint32_t v = sl.autos[size_t(f) * a.P + p];
+      const uint32_t v = va[p];
       const uint32_t s = v & 0xffu, j = v >> 8;
       const uint32_t rs = j ? (((s >> j) | (s << (m - j))) & uint32_t(n)) : s;
       ctx[p * 32] = j | ((rs ? uint32_t(n) - rs : 0u) << 8);
@@ -321,7 +327,7 @@ namespace {
 size_t align256s(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t llr, autos, hard, iters, flags, total;
+  size_t llr, hard, iters, flags, total;
 };
 
 Layout req_layout(const bch_server *s, int code, int F, int ld) {
@@ -330,8 +336,6 @@ Layout req_layout(const bch_server *s, int code, int F, int ld) {
   size_t off = 0;
   L.llr = off;
   off = align256s(off + size_t(F) * ld * 4);
-  L.autos = off;
-  off = align256s(off + size_t(F) * s->cfg.n_autos * 2);
   L.hard = off;
   off = align256s(off + size_t(F) * W64 * 8);
   L.iters = off;
@@ -401,7 +405,8 @@ bch_status admit(bch_server *s, bch_server::Req &r, bool *admitted) {
   unsigned char *base = s->arena + off;
   SrvSlot sl{};
   sl.llr = reinterpret_cast<const float *>(base + L.llr);
-  sl.autos = reinterpret_cast<const uint16_t *>(base + L.autos);
+  sl.seed = r.seed;
+  sl.frame0 = r.frame0;
   sl.hard = reinterpret_cast<uint64_t *>(base + L.hard);
   sl.iters = base + L.iters;
   sl.flags = base + L.flags;
@@ -415,12 +420,6 @@ bch_status admit(bch_server *s, bch_server::Req &r, bool *admitted) {
   sl.done = 0;
   cudaError_t e = cudaMemcpyAsync(const_cast<float *>(sl.llr), r.llr, size_t(r.F) * r.ld * 4, cudaMemcpyDefault,
                                   s->cst);
-  if (e == cudaSuccess) {
-    int ord = 1;
-    const int n = s->codes[r.code]->alg.n;
-    for (int x = 2 % n; x != 1; x = (2 * x) % n) ord++;
-    e = launch_draw_autos(n, ord, s->cfg.n_autos, r.seed, r.frame0, r.F, const_cast<uint16_t *>(sl.autos), s->cst);
-  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->slots_dev + r.slot, &sl, sizeof(sl), cudaMemcpyHostToDevice, s->cst);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->cst);
   if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("admission copies: ") + cudaGetErrorString(e));
@@ -564,6 +563,8 @@ bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
     sc_.std_rows = sc ? reinterpret_cast<const uint4 *>(sc->dc.rowmask) : nullptr;
     sc_.M = sc ? sc->alg.n - sc->alg.k : 0;
     sc_.has_osd = sc ? 1 : 0;
+    sc_.ord = 1;
+    for (int x = 2 % co->alg.n; x != 1; x = (2 * x) % co->alg.n) sc_.ord++;
     const int mw = co->dc.max_w;
     sc_.wb = mw <= 8 ? 8 : mw <= 16 ? 16 : mw <= 24 ? 24 : mw <= 32 ? 32 : mw <= 48 ? 48 : 0;
     if (!sc_.wb) {

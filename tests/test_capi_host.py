@@ -69,3 +69,11 @@ def test_bit_packing_roundtrip():
     rng = np.random.default_rng(0)
     bits = rng.integers(0, 2, (50, 127), dtype=np.uint8)
     assert np.array_equal(B.unpack_bits(B.pack_bits(bits), 127), bits)
+
+
+@pytest.mark.parametrize("msg", [0, 1, 2])
+def test_specialised_kernel_compiles_without_gpu(msg):
+    """The run-time specialised enhanced-NMS kernel of BCH(63,45) compiles for sm_103a
+    (NVRTC, no GPU) in every message format."""
+    report = B.nms_jit_check(63, 45, msg)
+    assert "registers" in report

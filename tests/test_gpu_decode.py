@@ -324,3 +324,29 @@ def test_jit_and_generic_kernels_agree(torch_cuda, msg, monkeypatch):
         ok = ~ambiguous_frames(llr, ref, n)
         assert np.array_equal(a["hard"][ok], b["hard"][ok])
         assert np.array_equal(a["iters"][ok], b["iters"][ok])
+
+
+@pytest.mark.parametrize("ebn0", [2.0, 4.0])
+def test_bch15_hybrid_fer_vs_exhaustive_ml(torch_cuda, ebn0):
+    """BCH(15,7) at 10^5 frames: the GPU hybrid decoder (NMS on H_o + OSD-2) reaches the
+    FER of exhaustive maximum-likelihood decoding over all 128 codewords (oracle)."""
+    torch = torch_cuda
+    n, k, F = 15, 7, 100_000
+    c, std = code(n, k), code(n, k, B.PCM_STANDARD)
+    cw, llr = frames(n, k, F, ebn0, 1507 + int(ebn0), ld=16)
+    autos = O.draw_autos(n, 3, 29, 0, F)
+    p = B.params(12, 0.78, osd_order=2)
+    hard = torch.zeros((F, 1), dtype=torch.int64, device="cuda")
+    it = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    fl = torch.zeros(F, dtype=torch.uint8, device="cuda")
+    B.hybrid_decode(c, std, p, to_dev(llr), autos_dev(autos), hard, it, fl)
+    torch.cuda.synchronize()
+    got = B.unpack_bits(hard.cpu().numpy(), n)
+    ml = O.ml(n, k, llr)
+    e_h = int(np.any(got != cw, axis=1).sum())
+    e_ml = int(np.any(ml != cw, axis=1).sum())
+    # ML is optimal on average; the hybrid may differ from it only on a small share
+    assert e_ml > 30
+    sd = np.sqrt(e_h + e_ml)
+    assert abs(e_h - e_ml) <= 3 * sd, (e_h, e_ml)
+    assert np.mean(np.any(got != ml, axis=1)) < 0.01
