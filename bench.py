@@ -402,7 +402,10 @@ def main():
     # ---- serving: mixed-code Poisson stream, server vs static batching
     serving = None
     if rank == 0 and args.serve_seconds > 0:
-        serving = run_serving(B, torch, dev, args.serve_seconds, args.serve_rate)
+        try:
+            serving = run_serving(B, torch, dev, args.serve_seconds, args.serve_rate)
+        except B.BchError as e:  # reported in the line; the decode throughput stands
+            serving = {"error": str(e)}
 
     # ---- training: per-iteration alpha_t of BCH(127,64) through the backward kernel
     training = None

@@ -76,3 +76,30 @@ def test_fp16_close_to_oracle(torch_cuda, nk, rescale):
     ref = O.nms_enhanced_q(c.dense(), llr, autos, 12, ALPHA, 1, rescale=rescale, threads=None)
     agree = np.all(g["hard"] == ref["hard"], axis=1) & (g["iters"] == ref["iters"])
     assert agree.mean() >= 0.99
+
+
+def test_fer_sweep_small(torch_cuda):
+    """The precision sweep: FP32 NMS FER equals a direct decode of the same frames, and
+    the FP16 / INT8 forms stay close to FP32 at 2 x 20 000 frames."""
+    torch = torch_cuda
+    from paper_2412_20828_gb300 import fer_sweep as FS
+    res = FS.run(codes=[(63, 45)], points=[3.0, 4.0], frames=20000, chunk=8192, hybrid=True)
+    e = res["codes"]["(63,45)"]["variants"]
+    # direct FP32 decode of point 0 (frame indices 0.., seed as the sweep draws them)
+    c = B.Code(63, 45)
+    llr = torch.empty((20000, 64), dtype=torch.float32, device="cuda")
+    cw = torch.empty((20000, 1), dtype=torch.int64, device="cuda")
+    aut = torch.empty((20000, 3), dtype=torch.int16, device="cuda")
+    B.gen_frames(c, 3.0, 3.0, 0x5EED, 0, llr, cw)
+    B.draw_automorphisms(63, 3, 0x5EED + 1, 0, aut)
+    hard = torch.empty((20000, 1), dtype=torch.int64, device="cuda")
+    B.nms_decode(c, B.params(12, 0.78), llr, aut, hard)
+    torch.cuda.synchronize()
+    fe = int((hard != cw).any(dim=1).sum())
+    assert e["fp32"]["nms"]["frame_errors"][0] == fe
+    for name in ("fp16", "int8", "int8_rescale"):
+        for stage in ("nms", "hybrid"):
+            a = np.array(e[name][stage]["frame_errors"], float)
+            b = np.array(e["fp32"][stage]["frame_errors"], float)
+            assert np.all(np.abs(a - b) <= 0.25 * b + 4 * np.sqrt(b + 1)), (name, stage, a, b)
+    assert "loss_db_vs_fp32" in e["int8"]["nms"]

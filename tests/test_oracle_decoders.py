@@ -382,3 +382,28 @@ def test_quantised_decoder_equals_fp64_on_exact_inputs(fmt):
         inr = np.abs(b["y"]) * 4 <= 31
         assert np.array_equal(a["y"][inr], b["y"][inr])
     assert np.array_equal(a["hard"], b["hard"])
+
+
+def test_osd2_matches_paper_printed_points():
+    """The oracle's order-2 OSD reaches the error rates the paper prints for OSD(2)
+    (Fig. 2, Fig. 3; golden tests/golden/osd2_printed_points.txt) within a band of
+    three standard deviations of our estimate plus 10% for the paper's unknown sample."""
+    rows = []
+    with open(os.path.join(GOLD, "osd2_printed_points.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                n, k, e, meas, val = line.split()[:5]
+                rows.append((int(n), int(k), float(e), meas, float(val)))
+    frames_for = {(63, 36): 40000, (63, 45): 12000, (127, 99): 6000}
+    for i, (n, k, e, meas, val) in enumerate(rows):
+        F = frames_for[(n, k)]
+        msg = synth.messages(F, k, 4300 + i)
+        cw = O.encode(n, k, msg)
+        llr = O.channel_llr(n, k, cw, synth.normals(F, n, 4300 + i), e)
+        dec, _ = O.osd(O.std_h(n, k), llr, 2, threads=None)
+        err = dec != cw
+        fe = int(err.any(axis=1).sum())
+        got = err.mean() if meas == "ber" else fe / F
+        band = 3.0 / np.sqrt(max(fe, 1)) + 0.10
+        assert fe >= 100, (n, k, e, fe)
+        assert abs(got / val - 1.0) <= band, (n, k, e, meas, got, val, band)
