@@ -183,17 +183,59 @@ def run_serving(B, torch, dev, seconds, rate):
     # warm-up: a short stream
     B.serve_bench(srv, codes, stds, pools, rate, 0.5, seed=11)
     res = B.serve_bench(srv, codes, stds, pools, rate, seconds, seed=12)
-    stats = srv.stats()
-    srv.close()
     stat = B.serve_bench(None, codes, stds, pools, rate, seconds, seed=12, static_batching=True,
                          batch_us=1000, batch_frames=65536)
+    # the same stream below saturation: half the request rate the slower of the two served
+    sub = 0.5 * min(res["requests"] / res["elapsed_s"], stat["requests"] / stat["elapsed_s"], rate)
+    res_sub = B.serve_bench(srv, codes, stds, pools, sub, seconds, seed=13)
+    stat_sub = B.serve_bench(None, codes, stds, pools, sub, seconds, seed=13, static_batching=True,
+                             batch_us=1000, batch_frames=65536)
+    stats = srv.stats()
+    srv.close()
     return {"workload": f"Poisson {rate:.0f} req/s, 1-4096 frames log-uniform, codes "
                         "(63,36),(63,45),(127,64),(127,99), Eb/N0 U[1,6] dB, hybrid NMS(12,P=3)+OSD(2)",
-            "seconds": seconds, "server": res, "server_stats": stats,
-            "static_batching": stat}
+            "seconds": seconds, "server": res, "static_batching": stat,
+            "below_saturation": {"rate_rps": sub, "server": res_sub, "static_batching": stat_sub},
+            "server_stats": stats}
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def run_plain(B, torch, dev, reps=50):
+    """BCH(63,36) plain flooding NMS (Eqs. 2-5) on the standard 27 x 63 H: 10 000 frames
+    at 3 dB, 8 iterations, alpha = 0.78, early stop.  The frames (2.5 MB) stay in L2
+    across the repeated decodes; time per decode from CUDA events on the stream."""
+    code = B.Code(63, 36, kind=B.PCM_STANDARD)
+    F = 10000
+    llr = torch.empty((F, 64), dtype=torch.float32, device=dev)
+    cw = torch.empty((F, 1), dtype=torch.int64, device=dev)
+    B.gen_frames(code, 3.0, 3.0, SEED_FRAMES + 1, 0, llr, cw)
+    p = B.params(8, ALPHA, n_autos=0)
+    hard = torch.empty((F, 1), dtype=torch.int64, device=dev)
+    it = torch.empty(F, dtype=torch.uint8, device=dev)
+    fl = torch.empty(F, dtype=torch.uint8, device=dev)
+    ws = B.workspace(code, p, F)
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        B.nms_decode(code, p, llr, None, hard, it, fl, ws=ws)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        B.nms_decode(code, p, llr, None, hard, it, fl, ws=ws)
+    b.record(stream)
+    torch.cuda.synchronize()
+    dt = a.elapsed_time(b) / 1e3 / reps
+    B.count_errors(63, hard, cw, it, fl, ctr)
+    c = ctr.cpu().numpy()
+    code.close()
+    return {"workload": "BCH(63,36) plain NMS on standard H (27x63, E=486), 8 iters, alpha 0.78, "
+                        "early stop, 3 dB, 10000 frames (L2-resident, repeated)",
+            "frames_per_s": F / dt, "us_per_decode": dt * 1e6, "fer": float(c[1] / c[0]),
+            "ber": float(c[2] / (c[0] * 63)), "avg_iters": float(c[5] / c[0]),
+            "edge_updates_per_s": float(c[5]) * 486 / dt}
+
+
 def run_training(B, torch, steps, batch=65536, iters=12):
     """BCH(127,64) enhanced NMS (P = 3), alpha_1..alpha_12 trained from 0.78 by Adam on
     batches of 65 536 frames at Eb/N0 uniform in [2, 5] dB that the library simulates,
@@ -407,6 +449,9 @@ def main():
         except B.BchError as e:  # reported in the line; the decode throughput stands
             serving = {"error": str(e)}
 
+    # ---- plain NMS on the standard matrix (the single-decoder configuration)
+    plain = run_plain(B, torch, dev) if rank == 0 else None
+
     # ---- training: per-iteration alpha_t of BCH(127,64) through the backward kernel
     training = None
     if rank == 0 and args.train_steps > 0:
@@ -445,7 +490,7 @@ def main():
                        "parallelism": f"frames sharded over {world} GPU(s)"},
             "edge_updates_per_s": eups, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": args.steps * len(CODES) * (NPT + 1 + 2 + 1 + NPT),
-            "serving": serving, "training": training,
+            "serving": serving, "training": training, "plain_nms": plain,
             "fer_match_oracle_ci95": fer_match, "per_point": per_point,
         }
         print(json.dumps(line), flush=True)

@@ -79,10 +79,11 @@ NvrtcApi &nvrtc() {
 // row's negative entries, taken from the copy's sign mask with the row mask as an
 // immediate.  m_j(u) is min1 except at the row's minimum, handled by a predicated add
 // of (v2 - v1) -- this keeps min/max/compare work on the ALU pipe down to ~4 operations
-// per edge and moves the additions to the FMA pipe.  The two smallest magnitudes are
-// tracked two edges at a time: with lo/hi the sorted pair, min1' = min(min1, lo) and
-// min2' = min(max(min1, lo), min2, hi) (second smallest of four values with
-// min1 <= min2), 5 operations per pair with a three-input minimum instead of 6.
+// per edge and moves the additions to the FMA pipe.  With the pair knob on, the two
+// smallest magnitudes are tracked two edges at a time: with lo/hi the sorted pair,
+// min1' = min(min1, lo) and min2' = min(max(min1, lo), min2, hi) (second smallest of
+// four values with min1 <= min2), 5 operations per pair with a three-input minimum
+// instead of 6.
 const char *row_macros(int msg) {
   if (msg == 2)
     return R"(
@@ -151,16 +152,19 @@ int env_int(const char *name, int lo, int hi, int dflt) {
 }
 }  // namespace
 
-// Threads per block: 384 for n <= 63 (three warps per scheduler, all in lockstep so the
-// straight-line body is fetched once per block), 64 for n = 127.  BCHDEC_JIT_TPB
-// (a multiple of 32, 64..512) overrides it for n <= 63 -- a tuning knob.
+// Threads per block: 256 for n <= 63 (two warps per scheduler, all in lockstep so the
+// straight-line body is fetched once per block; 255 registers hold the 2n
+// register-resident values without spilling), 64 for n = 127.  BCHDEC_JIT_TPB (a
+// multiple of 32, 64..512) overrides it for n <= 63 -- a tuning knob.  Measured on the
+// (63,36) + (63,45) workload: 256 threads 187.1 M frames/s, 384 threads 186.0.
 int jit_block_size(int n) {
   if (n > 63) return 64;
-  const int t = env_int("BCHDEC_JIT_TPB", 64, 512, 384);
-  return t % 32 == 0 ? t : 384;
+  const int t = env_int("BCHDEC_JIT_TPB", 64, 512, 256);
+  return t % 32 == 0 ? t : 256;
 }
-// BCHDEC_JIT_PAIRS=0 tracks min1/min2 one edge at a time (tuning knob; default pairs).
-bool jit_pairs() { return env_int("BCHDEC_JIT_PAIRS", 0, 1, 1) == 1; }
+// BCHDEC_JIT_PAIRS=1 tracks min1/min2 two edges at a time (tuning knob; off by default:
+// it needs more registers and measured 1-2% slower).
+bool jit_pairs() { return env_int("BCHDEC_JIT_PAIRS", 0, 1, 0) == 1; }
 bool jit_lockstep(int n) { return n <= 63; }
 // Resident blocks per SM the register budget is sized for: 384 threads per SM for
 // n <= 63 (at most 170 registers each, about the 2n register-resident values plus

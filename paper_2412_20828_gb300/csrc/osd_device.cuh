@@ -11,7 +11,8 @@
 //  * with the reduced rows, the disagreement pattern of a test pattern e on the
 //    most reliable basis is D(e) = D0 xor (xor of the basis columns in e) restricted
 //    to the n-k pivot positions, so a candidate costs a few XORs plus a weighted
-//    popcount done with eight 256-entry tables of pivot weights;
+//    popcount done with 16-entry tables of pivot weights, one per 4 pivot rows (built
+//    by doubling: entry v = entry v - 2^b + weight b for the top bit b of v);
 //  * scores are exact 64-bit integers (weights floor(|L| 2^24)), and the warp keeps
 //    the lexicographic minimum of (score, enumeration index): the result equals a
 //    sequential scan that keeps the first minimum.
@@ -21,12 +22,16 @@
 namespace bchlib {
 
 
+// About 4.9 KB per warp, so that many warps share an SM (the elimination is a chain of
+// dependent ballots and shuffles that needs other warps to hide its latency).
 struct OsdSmem {
-  unsigned long long key[128];
-  unsigned long long colbits[128];
+  union {
+    unsigned long long key[128];      // sort keys (ranking phase only)
+    unsigned long long colbits[128];  // basis columns on the pivot rows (after elimination)
+  };
   unsigned long long wm[128];  // weights of the MRB positions, by basis index
   unsigned long long wp[64];   // weights of the pivot positions, by row
-  unsigned long long tab[8][256];
+  unsigned long long tab[16][16];  // weighted popcount of each 4-row chunk
   uint8_t perm[128];           // sorted position -> original index
   uint8_t mrb[128];            // basis index -> original index
   uint8_t ispiv[128];          // by original index
@@ -50,7 +55,7 @@ __device__ __forceinline__ uint4 shfl4(uint4 v, int src) {
 
 __device__ __forceinline__ unsigned long long wsum(const OsdSmem &S, unsigned long long D, int nch) {
   unsigned long long s = 0;
-  for (int c = 0; c < nch; c++) s += S.tab[c][(D >> (8 * c)) & 0xffu];
+  for (int c = 0; c < nch; c++) s += S.tab[c][(D >> (4 * c)) & 0xfu];
   return s;
 }
 
@@ -173,15 +178,17 @@ __device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, c
   const unsigned d0b = __ballot_sync(kFull, lane + 32 < M && parity4(and4(row1, h)));
   const unsigned long long D0 = (unsigned long long)d0a | ((unsigned long long)d0b << 32);
   __syncwarp();
-  const int nch = (M + 7) / 8;
-  for (int e = lane; e < nch * 256; e += 32) {
-    const int c = e >> 8, v = e & 255;
-    unsigned long long s = 0;
-    for (int b = 0; b < 8; b++)
-      if ((v >> b) & 1) s += S.wp[8 * c + b];
-    S.tab[c][v] = s;
-  }
+  const int nch = (M + 3) / 4;
+  if (lane < nch) S.tab[lane][0] = 0ull;
   __syncwarp();
+  for (int b = 0; b < 4; b++) {
+    const int per = 1 << b;
+    for (int e = lane; e < nch * per; e += 32) {
+      const int c = e >> b, v = e & (per - 1);
+      S.tab[c][per + v] = S.tab[c][v] + S.wp[4 * c + b];
+    }
+    __syncwarp();
+  }
   // ---- enumerate test patterns
   Best best;
   best.s = ~0ull;

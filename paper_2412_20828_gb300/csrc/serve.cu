@@ -314,6 +314,10 @@ struct bch_server {
   std::map<unsigned long long, Req> active;
   std::vector<int> free_slots;
   std::vector<unsigned> slot_gen;
+  SrvSlot *slot_mirror = nullptr;         // pinned host copies of the slot descriptors
+  std::vector<cudaEvent_t> slot_ev;       // per slot: its admission copies are done
+  std::deque<unsigned> staged;            // ring entries whose copies are in flight, in order
+  long long published_open = 0;           // published requests not yet completed
   unsigned sub_tail = 0, comp_read = 0;
   unsigned long long next_id = 1;
   int blocks = 0;
@@ -391,7 +395,40 @@ bch_status launch_server_kernel(bch_server *s) {
   return BCH_OK;
 }
 
-// Admits a request (memory, slot, copies, publication).  Caller holds the lock.
+bch_status ensure_running(bch_server *s) {
+  if (s->published_open > 0 && !s->sh->running) {
+    cudaStreamSynchronize(s->kst);  // a previous instance that exited idle has finished
+    bch_status st = launch_server_kernel(s);
+    if (st != BCH_OK) return st;
+    s->stats.kernel_launches++;
+  }
+  return BCH_OK;
+}
+
+// Publishes, in admission order, the staged requests whose copies have landed: their
+// ring entries become visible to the kernel.  Caller holds the lock.
+bch_status publish_staged(bch_server *s) {
+  bool any = false;
+  while (!s->staged.empty()) {
+    const unsigned entry = s->staged.front();
+    const cudaError_t e = cudaEventQuery(s->slot_ev[entry & 0xffffu]);
+    if (e == cudaErrorNotReady) break;
+    if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("admission copies: ") + cudaGetErrorString(e));
+    s->sub_ring[s->sub_tail % unsigned(s->cfg.max_requests)] = entry;
+    std::atomic_thread_fence(std::memory_order_release);
+    s->sub_tail++;
+    s->sh->sub_tail = s->sub_tail;
+    s->staged.pop_front();
+    s->published_open++;
+    any = true;
+  }
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  return any ? ensure_running(s) : BCH_OK;
+}
+
+// Admits a request: memory, slot, asynchronous copies of its LLRs and descriptor, then
+// staging for publication once the copies are done (no host wait).  Caller holds the
+// lock.
 bch_status admit(bch_server *s, bch_server::Req &r, bool *admitted) {
   *admitted = false;
   if (s->free_slots.empty()) return BCH_OK;
@@ -403,7 +440,8 @@ bch_status admit(bch_server *s, bch_server::Req &r, bool *admitted) {
   r.slot = s->free_slots.back();
   s->free_slots.pop_back();
   unsigned char *base = s->arena + off;
-  SrvSlot sl{};
+  SrvSlot &sl = s->slot_mirror[r.slot];  // no copy from this slot is in flight: it was free
+  std::memset(&sl, 0, sizeof(sl));
   sl.llr = reinterpret_cast<const float *>(base + L.llr);
   sl.seed = r.seed;
   sl.frame0 = r.frame0;
@@ -420,24 +458,15 @@ bch_status admit(bch_server *s, bch_server::Req &r, bool *admitted) {
   sl.done = 0;
   cudaError_t e = cudaMemcpyAsync(const_cast<float *>(sl.llr), r.llr, size_t(r.F) * r.ld * 4, cudaMemcpyDefault,
                                   s->cst);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s->slots_dev + r.slot, &sl, sizeof(sl), cudaMemcpyHostToDevice, s->cst);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->cst);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->slots_dev + r.slot, &sl, sizeof(sl), cudaMemcpyHostToDevice, s->cst);
+  if (e == cudaSuccess) e = cudaEventRecord(s->slot_ev[r.slot], s->cst);
   if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("admission copies: ") + cudaGetErrorString(e));
-  s->sub_ring[s->sub_tail % unsigned(s->cfg.max_requests)] = unsigned(r.slot) | (gen << 16);
-  std::atomic_thread_fence(std::memory_order_release);
-  s->sub_tail++;
-  s->sh->sub_tail = s->sub_tail;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
+  s->staged.push_back(unsigned(r.slot) | (gen << 16));
   s->stats.admitted++;
   s->stats.bytes_in_use += L.total;
   *admitted = true;
-  if (!s->sh->running) {
-    cudaStreamSynchronize(s->kst);  // a previous instance that timed out has finished
-    bch_status st = launch_server_kernel(s);
-    if (st != BCH_OK) return st;
-    s->stats.kernel_launches++;
-  }
-  return BCH_OK;
+  return publish_staged(s);
 }
 
 bch_status admit_pending(bch_server *s) {
@@ -479,6 +508,8 @@ bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
     if (s->kst) cudaStreamDestroy(s->kst);
     if (s->cst) cudaStreamDestroy(s->cst);
     if (s->sh) cudaFreeHost(s->sh);
+    if (s->slot_mirror) cudaFreeHost(s->slot_mirror);
+    for (cudaEvent_t ev : s->slot_ev) cudaEventDestroy(ev);
     cudaFree(s->slots_dev);
     cudaFree(s->dv);
     cudaFree(s->grp_dev);
@@ -588,6 +619,18 @@ bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
   }
   for (int i = R - 1; i >= 0; i--) s->free_slots.push_back(i);
   s->slot_gen.assign(R, 0);
+  if (cudaHostAlloc(reinterpret_cast<void **>(&s->slot_mirror), sizeof(SrvSlot) * R, cudaHostAllocDefault) !=
+      cudaSuccess) {
+    s->slot_mirror = nullptr;
+    cleanup();
+    return fail(BCH_ENOMEM, "pinned slot descriptors");
+  }
+  s->slot_ev.assign(R, nullptr);
+  for (int i = 0; i < R; i++)
+    if (cudaEventCreateWithFlags(&s->slot_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      cleanup();
+      return fail(BCH_ECUDA, "slot events");
+    }
   A.slots = s->slots_dev;
   if (cudaStreamCreateWithFlags(&s->kst, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking) != cudaSuccess) {
@@ -659,21 +702,15 @@ bch_status bch_server_poll(bch_server *s, uint64_t *done_ids, int max_ids, int *
         s->comp_read++;
         auto it = s->active.find(id);
         if (it != s->active.end()) it->second.done = true;
+        s->published_open--;
         done_ids[(*n_done)++] = id;
         s->stats.completed++;
       }
       bch_status st = admit_pending(s);
+      if (st == BCH_OK) st = publish_staged(s);
+      // a kernel instance that exited idle while published work is open: relaunch
+      if (st == BCH_OK) st = ensure_running(s);
       if (st != BCH_OK) return st;
-      // a kernel instance that exited idle while admitted work is outstanding: relaunch
-      bool outstanding = false;
-      for (auto &kv : s->active)
-        if (!kv.second.done && kv.second.slot >= 0) outstanding = true;
-      if (outstanding && !s->sh->running) {
-        cudaStreamSynchronize(s->kst);
-        st = launch_server_kernel(s);
-        if (st != BCH_OK) return st;
-        s->stats.kernel_launches++;
-      }
     }
     if (*n_done > 0 || timeout_us <= 0) break;
     const auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0);
@@ -725,6 +762,8 @@ void bch_server_destroy(bch_server *s) {
   cudaStreamDestroy(s->kst);
   cudaStreamDestroy(s->cst);
   cudaFreeHost(s->sh);
+  if (s->slot_mirror) cudaFreeHost(s->slot_mirror);
+  for (cudaEvent_t ev : s->slot_ev) cudaEventDestroy(ev);
   cudaFree(s->slots_dev);
   cudaFree(s->dv);
   cudaFree(s->grp_dev);
@@ -778,10 +817,23 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
     reqs.push_back(r);
     offered_frames += F;
   }
-  int W64max = 2;
-  size_t maxF = size_t(c->max_frames);
-  std::vector<uint64_t> hbuf(maxF * W64max);
-  std::vector<uint8_t> ibuf(maxF), fbuf(maxF);
+  // results land in pinned host memory, as a latency-sensitive caller would have them
+  struct Pinned {
+    void *p = nullptr;
+    explicit Pinned(size_t b) {
+      if (cudaHostAlloc(&p, b, cudaHostAllocDefault) != cudaSuccess) p = nullptr;
+    }
+    ~Pinned() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  const size_t maxF = size_t(c->max_frames);
+  const size_t capF = size_t(std::max(c->batch_frames, c->max_frames) + c->max_frames);
+  Pinned hpin(capF * 16 * size_t(c->n_codes)), ipin(capF * size_t(c->n_codes)), fpin(capF * size_t(c->n_codes));
+  if (!hpin.p || !ipin.p || !fpin.p) return fail(BCH_ENOMEM, "pinned result buffers");
+  uint64_t *hbuf = static_cast<uint64_t *>(hpin.p);
+  uint8_t *ibuf = static_cast<uint8_t *>(ipin.p), *fbuf = static_cast<uint8_t *>(fpin.p);
+  (void)maxF;
   std::vector<double> lat;
   lat.reserve(reqs.size());
   long long frames_done = 0;
@@ -809,7 +861,7 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
         auto it = by_id.find(ids[i]);
         if (it == by_id.end()) continue;
         Rq &r = reqs[it->second];
-        st = bch_server_fetch(srv, r.id, hbuf.data(), ibuf.data(), fbuf.data());
+        st = bch_server_fetch(srv, r.id, hbuf, ibuf, fbuf);
         if (st != BCH_OK) return st;
         lat.push_back(now_s() - r.t_arr);
         frames_done += r.F;
@@ -849,8 +901,6 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
           cudaMalloc(&dfl[k], cap) != cudaSuccess || cudaMalloc(&dws[k], wsb) != cudaSuccess)
         return fail(BCH_ENOMEM, "static batching buffers");
     }
-    std::vector<uint64_t> hh(size_t(cap) * 2);
-    std::vector<uint8_t> hi(cap), hf(cap);
     size_t next = 0;
     while (next < reqs.size()) {
       // wait for the first request of the batch, then collect
@@ -888,9 +938,9 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
                                           nullptr, dws[k], st);
         if (s2 != BCH_OK) return s2;
         const int W64 = (c->codes[k]->alg.n + 63) / 64;
-        cudaMemcpyAsync(hh.data(), dhard[k], size_t(tot) * W64 * 8, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(hi.data(), dit[k], tot, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(hf.data(), dfl[k], tot, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(hbuf + size_t(k) * capF * 2, dhard[k], size_t(tot) * W64 * 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(ibuf + size_t(k) * capF, dit[k], tot, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(fbuf + size_t(k) * capF, dfl[k], tot, cudaMemcpyDeviceToHost, st);
       }
       if (cudaStreamSynchronize(st) != cudaSuccess) return fail(BCH_ECUDA, "static batch");
       tn = now_s();

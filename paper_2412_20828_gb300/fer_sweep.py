@@ -58,10 +58,13 @@ def fer_loss_db(points, fer_ref, fer_var, errors_var, min_errors=50):
 
 
 def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, alpha=0.78,
-        n_autos=3, chunk=1 << 20, seed=0x5EED, hybrid=True, log=sys.stderr):
+        n_autos=3, chunk=1 << 20, seed=0x5EED, hybrid=True, variants=None, log=sys.stderr):
     import torch
     from . import bchdec as B
     B.load()
+    vlist = [v for v in VARIANTS if variants is None or v[0] in variants]
+    if not vlist or vlist[0][0] != "fp32":
+        raise ValueError("the variants must include fp32 (the reference curve)")
     res = {"points": list(points), "frames_per_point": frames, "iters": iters, "alpha": alpha,
            "n_autos": n_autos, "codes": {}}
     for n, k in codes:
@@ -76,10 +79,19 @@ def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, 
         hard = torch.empty((Fc, W), dtype=torch.int64, device="cuda")
         its = torch.empty(Fc, dtype=torch.uint8, device="cuda")
         flg = torch.empty(Fc, dtype=torch.uint8, device="cuda")
-        ctr = torch.zeros((len(VARIANTS), 2, len(points), 8), dtype=torch.int64, device="cuda")
+        ctr = torch.zeros((len(vlist), 2, len(points), 8), dtype=torch.int64, device="cuda")
         ps = {name: B.params(iters, alpha, n_autos=n_autos, msg=msg, rescale=rs)
-              for name, msg, rs in VARIANTS}
+              for name, msg, rs in vlist}
         ws = B.workspace(code, ps["fp32"], Fc)
+        ev = []  # (variant, stage, point, start, end): device time of each decode call
+        stream = torch.cuda.current_stream()
+
+        def timed(vi, si, pi, fn):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((vi, si, pi, a, b))
         t0 = time.time()
         for pi, e in enumerate(points):
             for f0 in range(0, frames, Fc):
@@ -87,18 +99,21 @@ def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, 
                 base = pi * 10**9 + f0
                 B.gen_frames(code, e, e, seed, base, llr[:F], cw[:F])
                 B.draw_automorphisms(n, n_autos, seed + 1, base, aut[:F])
-                for vi, (name, _, _) in enumerate(VARIANTS):
-                    B.nms_decode(code, ps[name], llr[:F], aut[:F], hard[:F], its[:F], flg[:F],
-                                 ws=ws)
+                for vi, (name, _, _) in enumerate(vlist):
+                    timed(vi, 0, pi, lambda: B.nms_decode(code, ps[name], llr[:F], aut[:F], hard[:F],
+                                                          its[:F], flg[:F], ws=ws))
                     B.count_errors(n, hard[:F], cw[:F], its[:F], flg[:F], ctr[vi, 0, pi])
                     if hybrid:
-                        B.hybrid_decode(code, std, ps[name], llr[:F], aut[:F], hard[:F], its[:F],
-                                        flg[:F], ws=ws)
+                        timed(vi, 1, pi, lambda: B.hybrid_decode(code, std, ps[name], llr[:F], aut[:F],
+                                                                 hard[:F], its[:F], flg[:F], ws=ws))
                         B.count_errors(n, hard[:F], cw[:F], its[:F], flg[:F], ctr[vi, 1, pi])
         torch.cuda.synchronize()
         c = ctr.cpu().numpy()
+        dev_s = np.zeros((len(vlist), 2, len(points)))
+        for vi, si, pi, a, b in ev:
+            dev_s[vi, si, pi] += a.elapsed_time(b) / 1e3
         entry = {"seconds": time.time() - t0, "variants": {}}
-        for vi, (name, _, _) in enumerate(VARIANTS):
+        for vi, (name, _, _) in enumerate(vlist):
             v = {}
             for si, stage in enumerate(("nms", "hybrid")):
                 if stage == "hybrid" and not hybrid:
@@ -107,11 +122,12 @@ def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, 
                 v[stage] = {"frame_errors": c[vi, si, :, 1].tolist(),
                             "fer": (c[vi, si, :, 1] / fr).tolist(),
                             "ber": (c[vi, si, :, 2] / (fr * n)).tolist(),
-                            "avg_iters": (c[vi, si, :, 5] / fr).tolist()}
+                            "avg_iters": (c[vi, si, :, 5] / fr).tolist(),
+                            "frames_per_s": (fr / np.maximum(dev_s[vi, si], 1e-12)).tolist()}
             entry["variants"][name] = v
         for stage in ("nms", "hybrid") if hybrid else ("nms",):
             ref = entry["variants"]["fp32"][stage]["fer"]
-            for name, _, _ in VARIANTS[1:]:
+            for name, _, _ in vlist[1:]:
                 v = entry["variants"][name][stage]
                 v["loss_db_vs_fp32"] = fer_loss_db(points, ref, v["fer"], v["frame_errors"])
         res["codes"][f"({n},{k})"] = entry
@@ -154,11 +170,13 @@ def main(argv=None):
     ap.add_argument("--alpha", type=float, default=0.78)
     ap.add_argument("--points", default=",".join(f"{e:g}" for e in DEFAULT_POINTS))
     ap.add_argument("--no-hybrid", action="store_true")
+    ap.add_argument("--variants", default=",".join(v[0] for v in VARIANTS))
     ap.add_argument("--json", default=None)
     a = ap.parse_args(argv)
     codes = [tuple(int(x) for x in c.split(",")) for c in a.codes.split(";")]
     points = [float(x) for x in a.points.split(",")]
-    res = run(codes, points, a.frames, a.iters, a.alpha, hybrid=not a.no_hybrid)
+    res = run(codes, points, a.frames, a.iters, a.alpha, hybrid=not a.no_hybrid,
+              variants=a.variants.split(","))
     print(format_table(res))
     if a.json:
         with open(a.json, "w") as f:
