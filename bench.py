@@ -36,6 +36,12 @@ P_AUTOS, ITERS, ALPHA, OSD_ORDER = 3, 12, 0.78, 2
 SEED_FRAMES, SEED_AUTOS = 20241230, 0x5EED
 METRIC = "frames/s & edge-updates/s on 1 GB300 at oracle-matched FER; served p50/p99 latency"
 LANE_OPS_PER_EDGE = 8  # min1/min2 (3), sign (1), output select (2), accumulate (1), gather (1)
+# DRAM bytes per decoded frame of the specialised NMS kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a 1.1 M-frame BCH(63,36) launch:
+# 288.35 MB + 10.28 MB.  Traffic grows with the frames a launch decodes (each frame's
+# LLRs are read once, its results written once), so a launch's traffic is this figure
+# times its frames.  Set to None when the kernel changes until it is re-captured.
+JIT_DRAM_BYTES_PER_FRAME = (288.35e6 + 10.28e6) / 1.1e6
 
 
 def measured_peaks():
@@ -271,6 +277,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="duration of the serving stream (0 skips serving)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--no-plain", action="store_true", help="skip the single-decoder leg")
     ap.add_argument("--train-steps", type=int, default=20,
                     help="Adam steps of the BCH(127,64) alpha_t training leg (0 skips it)")
     args = ap.parse_args()
@@ -405,8 +412,12 @@ def main():
     achieved = edge_updates * LANE_OPS_PER_EDGE / nms_time
     kinfo = states[0]["code"].kernel_info(msg, P_AUTOS)
     kname = "bch_nms_jit" if kinfo == "jit" else "nms_enhanced_kernel"
+    traffic = None
+    if kinfo == "jit" and JIT_DRAM_BYTES_PER_FRAME is not None:
+        traffic = JIT_DRAM_BYTES_PER_FRAME * F  # bytes per launch (one code, F frames)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lane_ops / 1e12,
-                "unit": "Tlane-op/s", "frac": achieved / peak_lane_ops, "traffic": None,
+                "unit": "Tlane-op/s", "frac": achieved / peak_lane_ops, "traffic": traffic,
+                "traffic_unit": "bytes per launch", "algorithmic_bytes_per_launch": F * (63 * 4 + 6 + 10),
                 "kernel": kname, "kernel_info": kinfo, "lane_ops_per_edge_update": LANE_OPS_PER_EDGE,
                 "edge_updates_per_s": eups, "nms_ms_per_step": nms_time * 1e3,
                 "peak_basis": f"{sms} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock under load)"}
@@ -450,7 +461,7 @@ def main():
             serving = {"error": str(e)}
 
     # ---- plain NMS on the standard matrix (the single-decoder configuration)
-    plain = run_plain(B, torch, dev) if rank == 0 else None
+    plain = run_plain(B, torch, dev) if rank == 0 and not args.no_plain else None
 
     # ---- training: per-iteration alpha_t of BCH(127,64) through the backward kernel
     training = None
