@@ -320,6 +320,13 @@ bool jit_compile_check(const bch_code *c, int msg, std::string *log) {
     return false;
   }
   const std::string src = jit_source(c, msg);
+  // BCHDEC_JIT_DUMP=<file>: also write the generated source there (a debugging aid)
+  if (const char *dump = std::getenv("BCHDEC_JIT_DUMP")) {
+    if (FILE *fp = std::fopen(dump, "w")) {
+      std::fwrite(src.data(), 1, src.size(), fp);
+      std::fclose(fp);
+    }
+  }
   nvrtcProgram prog = nullptr;
   if (api.create(&prog, src.c_str(), "bch_nms_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
     *log = "nvrtcCreateProgram failed";

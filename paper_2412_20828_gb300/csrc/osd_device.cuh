@@ -200,12 +200,22 @@ __device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, c
       consider(best, S.wm[x] + wsum(S, D0 ^ S.colbits[x], nch), uint32_t(1 + x), uint32_t(x + 1));
   }
   if (order >= 2) {
+    // Exact pruning.  A candidate's score is at least wm[x] + wm[y] (all weights are
+    // non-negative) and wm ascends with the basis index (reliability order).  Every
+    // weight-2 candidate comes after the weight <= 1 ones in the enumeration, and a
+    // lane's earlier candidates come before its later ones, so a candidate whose bound
+    // reaches either best can at most tie it with a larger index: it cannot be chosen.
+    unsigned long long bound1 = best.s;
+    for (int off = 16; off > 0; off >>= 1) bound1 = min(bound1, __shfl_xor_sync(kFull, bound1, off));
     for (int x = 0; x + 1 < K; x++) {
-      const unsigned long long Da = D0 ^ S.colbits[x];
       const unsigned long long wa = S.wm[x];
+      if (wa + S.wm[x + 1] >= bound1) break;  // no pair (x' >= x, y > x') can win
+      const unsigned long long Da = D0 ^ S.colbits[x];
       const uint32_t base = uint32_t(1 + K) + uint32_t(x * K - x * (x + 1) / 2);
       for (int y = x + 1 + lane; y < K; y += 32) {
-        const unsigned long long s = wa + S.wm[y] + wsum(S, Da ^ S.colbits[y], nch);
+        const unsigned long long lb = wa + S.wm[y];
+        if (lb >= bound1 || lb >= best.s) break;  // later y only raise the bound
+        const unsigned long long s = lb + wsum(S, Da ^ S.colbits[y], nch);
         consider(best, s, base + uint32_t(y - x - 1), uint32_t(x + 1) | (uint32_t(y + 1) << 8));
       }
     }
