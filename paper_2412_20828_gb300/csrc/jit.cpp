@@ -13,6 +13,8 @@
 // Compiled with NVRTC (loaded with dlopen, so the library still loads on machines
 // without it) for sm_103a and loaded with cudaLibraryLoadData; cached per source text.
 #include <dlfcn.h>
+#include <sys/stat.h>
+#include <unistd.h>
 #include <nvrtc.h>
 
 #include <algorithm>
@@ -97,6 +99,7 @@ const char *row_macros(int msg) {
   const int c2_ = __double2int_rn(double(alpha) * double(m2_)); \
   const bool neg_ = (SG); const int v1_ = neg_ ? -c1_ : c1_; const int dv_ = (neg_ ? -c2_ : c2_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
+#define BCH_R2F(u) BCH_R2(u)
 #define BCH_RE }
 #define BCH_FIN(u) ((z[u] < 0) ? -BCH_SV(u) : BCH_SV(u))
 )";
@@ -113,6 +116,8 @@ const char *row_macros(int msg) {
   const float v1_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m1_))), sg_); \
   const float dv_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m2_))), sg_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
+#define BCH_R2F(u) { const float p_ = (fabsf(z[u]) - m1_) * 0x1p100f; \
+  BCH_SV(u) = __fmaf_rn(dv_, __saturatef(__fmaf_rn(-p_, 0x1p100f, 1.0f)), BCH_SV(u) + v1_); }
 #define BCH_RE }
 #define BCH_FIN(u) flip_sign(BCH_SV(u), __float_as_uint(z[u]))
 )";
@@ -127,6 +132,8 @@ const char *row_macros(int msg) {
 #define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
   const float v1_ = flip_sign(alpha * m1_, sg_); const float dv_ = flip_sign(alpha * m2_, sg_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
+#define BCH_R2F(u) { const float p_ = (fabsf(z[u]) - m1_) * 0x1p100f; \
+  BCH_SV(u) = __fmaf_rn(dv_, __saturatef(__fmaf_rn(-p_, 0x1p100f, 1.0f)), BCH_SV(u) + v1_); }
 #define BCH_RE }
 #define BCH_FIN(u) flip_sign(BCH_SV(u), __float_as_uint(z[u]))
 )";
@@ -165,6 +172,12 @@ int jit_block_size(int n) {
 // BCHDEC_JIT_PAIRS=1 tracks min1/min2 two edges at a time (tuning knob; off by default:
 // it needs more registers and measured 1-2% slower).
 bool jit_pairs() { return env_int("BCHDEC_JIT_PAIRS", 0, 1, 0) == 1; }
+// Percentage of output-pass edges emitted in the compare-free form: with t = |z| - min1
+// (>= 0), g = sat(1 - (t 2^100) 2^100) is exactly 1 when t = 0 and 0 otherwise
+// (denormals included: t >= 2^-149), and fma(dv, g, S + v1) rounds like the
+// predicated form (S + v1) + dv.  Five FMA-pipe operations replace one ALU compare and
+// two additions.  BCHDEC_JIT_FMA_PCT (0..100) is a tuning knob.
+int jit_fma_percent() { return env_int("BCHDEC_JIT_FMA_PCT", 0, 100, 0); }
 bool jit_lockstep(int n) { return n <= 63; }
 // Resident blocks per SM the register budget is sized for: 384 threads per SM for
 // n <= 63 (at most 170 registers each, about the 2n register-resident values plus
@@ -215,6 +228,11 @@ std::string jit_source(const bch_code *c, int msg) {
     << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) ng[u >> 5] |= "
     << (msg == 2 ? "(uint32_t(z[u]) >> 31)" : "(__float_as_uint(z[u]) >> 31)") << " << (u & 31);\n";
   // rows, grouped by weight like the device image
+  const int fma_pct = jit_fma_percent();
+  int fma_acc = 0;
+  // n = 127: a compiler fence after each row keeps the scheduler from overlapping the
+  // shared-memory row sums of many rows while 127 z values are live (fewer spills)
+  const bool fence = env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, n > 63 ? 1 : 0) == 1;
   for (const Row &row : c->rows) {
     std::vector<int> cols;
     for (int u = 0; u < n; u++)
@@ -241,8 +259,15 @@ std::string jit_source(const bch_code *c, int msg) {
     for (; pairs && e + 1 < cols.size(); e += 2) o << " BCH_R1P(" << cols[e] << ", " << cols[e + 1] << ")";
     for (; e < cols.size(); e++) o << " BCH_R1(" << cols[e] << ")";
     o << " BCH_RM(" << sg.str() << ")";
-    for (int u : cols) o << " BCH_R2(" << u << ")";
-    o << " BCH_RE\n";
+    // output pass: a share of the edges use the compare-free form (FMA pipe) so that
+    // the ALU and FMA pipes carry similar loads; both forms round identically
+    for (size_t q = 0; q < cols.size(); q++) {
+      fma_acc += fma_pct;
+      const bool f = fma_acc >= 100;
+      if (f) fma_acc -= 100;
+      o << (f ? " BCH_R2F(" : " BCH_R2(") << cols[q] << ")";
+    }
+    o << " BCH_RE" << (fence ? " asm volatile(\"\" ::: \"memory\");" : "") << "\n";
   }
   o << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) {\n"
     << "      const uint32_t i = addmod(bfe32(uint32_t(u) | (uint32_t(u) << " << m << "), jr, " << m
@@ -255,8 +280,76 @@ std::string jit_source(const bch_code *c, int msg) {
   return o.str();
 }
 
-// Returns the specialised kernel for (code, msg), compiling it on first use; on
-// failure returns nullptr and sets *err.
+// ---- on-disk cache of compiled kernels: <dir>/bchdec-jit-<hash>.cubin, keyed by the
+// source text, the compile options and the NVRTC version.  Directory:
+// BCHDEC_JIT_CACHE_DIR, else $XDG_CACHE_HOME/bchdec, else $HOME/.cache/bchdec;
+// BCHDEC_JIT_CACHE_DIR=off disables the cache.
+static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+static std::string cache_dir() {
+  const char *d = std::getenv("BCHDEC_JIT_CACHE_DIR");
+  if (d) return std::strcmp(d, "off") == 0 ? std::string() : std::string(d);
+  if (const char *x = std::getenv("XDG_CACHE_HOME")) return std::string(x) + "/bchdec";
+  if (const char *h = std::getenv("HOME")) return std::string(h) + "/.cache/bchdec";
+  return std::string();
+}
+
+static std::string cache_path(const std::string &src, const char *const *opts, int nopt) {
+  const std::string dir = cache_dir();
+  if (dir.empty()) return dir;
+  uint64_t h = fnv1a(src.data(), src.size());
+  for (int i = 0; i < nopt; i++) h = fnv1a(opts[i], std::strlen(opts[i]), h);
+  int major = 0, minor = 0;
+  using VersionFn = nvrtcResult (*)(int *, int *);
+  if (void *lib = dlopen("libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL)) {
+    if (auto fn = reinterpret_cast<VersionFn>(dlsym(lib, "nvrtcVersion"))) fn(&major, &minor);
+  }
+  const int ver[2] = {major, minor};
+  h = fnv1a(ver, sizeof(ver), h);
+  char name[64];
+  std::snprintf(name, sizeof(name), "/bchdec-jit-%016llx.cubin", (unsigned long long)h);
+  return dir + name;
+}
+
+static bool read_file(const std::string &path, std::vector<char> *out) {
+  FILE *fp = std::fopen(path.c_str(), "rb");
+  if (!fp) return false;
+  std::fseek(fp, 0, SEEK_END);
+  const long len = std::ftell(fp);
+  std::fseek(fp, 0, SEEK_SET);
+  bool ok = len > 0;
+  if (ok) {
+    out->resize(size_t(len));
+    ok = std::fread(out->data(), 1, size_t(len), fp) == size_t(len);
+  }
+  std::fclose(fp);
+  return ok;
+}
+
+static void write_file_atomic(const std::string &path, const std::vector<char> &data) {
+  const std::string dir = path.substr(0, path.rfind('/'));
+  // create the directory and its parents (best effort)
+  for (size_t pos = 1; pos != std::string::npos;) {
+    pos = dir.find('/', pos + 1);
+    mkdir(dir.substr(0, pos).c_str(), 0755);
+  }
+  char tmp[64];
+  std::snprintf(tmp, sizeof(tmp), ".tmp.%d", int(getpid()));
+  const std::string tpath = path + tmp;
+  FILE *fp = std::fopen(tpath.c_str(), "wb");
+  if (!fp) return;
+  const bool ok = std::fwrite(data.data(), 1, data.size(), fp) == data.size();
+  std::fclose(fp);
+  if (ok) std::rename(tpath.c_str(), path.c_str());
+  else std::remove(tpath.c_str());
+}
+
+// Returns the specialised kernel for (code, msg), compiling it on first use (or
+// loading it from the on-disk cache); on failure returns nullptr and sets *err.
 cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
   const std::string src = jit_source(c, msg);
   std::shared_ptr<Compiled> cp;
@@ -271,15 +364,23 @@ cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
   }
   cp = std::make_shared<Compiled>();
   NvrtcApi &api = nvrtc();
-  if (!api.ok) {
+  const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-I/usr/local/cuda/include",
+                        "-lineinfo"};
+  const std::string cache_file = cache_path(src, opts, 4);
+  std::vector<char> cached;
+  if (!cache_file.empty() && read_file(cache_file, &cached) &&
+      cudaLibraryLoadData(&cp->lib, cached.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) == cudaSuccess &&
+      cudaLibraryGetKernel(&cp->kernel, cp->lib, "bch_nms_jit") == cudaSuccess) {
+    // loaded a kernel compiled earlier from the same source
+  } else if (!api.ok) {
+    cp->kernel = nullptr;
     cp->err = api.err;
   } else {
+    cp->kernel = nullptr;
     nvrtcProgram prog = nullptr;
     if (api.create(&prog, src.c_str(), "bch_nms_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
       cp->err = "nvrtcCreateProgram failed";
     } else {
-      const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-I/usr/local/cuda/include",
-                            "-lineinfo"};
       const nvrtcResult r = api.compile(prog, 4, opts);
       if (r != NVRTC_SUCCESS) {
         size_t ls = 0;
@@ -298,6 +399,8 @@ cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
         if (e != cudaSuccess) {
           cp->kernel = nullptr;
           cp->err = std::string("loading the compiled kernel: ") + cudaGetErrorString(e);
+        } else if (!cache_file.empty()) {
+          write_file_atomic(cache_file, cubin);
         }
       }
       api.destroy(&prog);

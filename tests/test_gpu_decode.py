@@ -326,6 +326,30 @@ def test_jit_and_generic_kernels_agree(torch_cuda, msg, monkeypatch):
         assert np.array_equal(a["iters"][ok], b["iters"][ok])
 
 
+@pytest.mark.parametrize("msg", [B.MSG_FP32, B.MSG_FP16])
+def test_compare_free_edge_form_is_bit_identical(torch_cuda, msg, monkeypatch):
+    """The specialised kernel's two forms of the min2 correction -- predicated add after
+    a compare, and fma(dv, sat(1 - (t 2^100) 2^100), S + v1) -- round identically, so
+    kernels built with either form give the same bits (hard, iterations, final y)."""
+    n, k = 63, 45
+    c = code(n, k)
+    F = 3000
+    cw, llr = frames(n, k, F, 2.5, 4321, ld=64)
+    # include exact ties and tiny magnitudes (denormal differences t)
+    llr[:50, :8] = np.float32(1.5)
+    llr[50:100, :8] = np.float32(1e-40)
+    autos = O.draw_autos(n, 3, 88, 0, F)
+    monkeypatch.setenv("BCHDEC_JIT_FMA_PCT", "0")
+    a = run_nms(torch_cuda, c, llr, autos, 12, 0.78, msg=msg)
+    monkeypatch.setenv("BCHDEC_JIT_FMA_PCT", "100")
+    b = run_nms(torch_cuda, c, llr, autos, 12, 0.78, msg=msg)
+    monkeypatch.setenv("BCHDEC_JIT_FMA_PCT", "50")
+    d = run_nms(torch_cuda, c, llr, autos, 12, 0.78, msg=msg)
+    for key in ("hard", "iters", "flags", "y"):
+        assert np.array_equal(a[key], b[key]), key
+        assert np.array_equal(a[key], d[key]), key
+
+
 @pytest.mark.parametrize("ebn0", [2.0, 4.0])
 def test_bch15_hybrid_and_osd_vs_exhaustive_ml(torch_cuda, ebn0):
     """BCH(15,7) at 10^5 frames against exhaustive maximum-likelihood decoding over all
