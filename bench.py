@@ -396,10 +396,14 @@ def main():
         E = st["code"].edges
         for pi, e in enumerate(POINTS):
             c = ctr[pi]
+            # iterations used by the NMS stage (last timed step; reporting only)
+            hist = torch.bincount(st["iters"][pi * Bp:(pi + 1) * Bp].long(), minlength=ITERS + 1)
+            lo, hi = clopper_pearson(int(c[1]), int(c[0]))
             per_point.append({"code": f"({st['n']},{st['k']})", "ebn0": e, "frames": int(c[0]),
-                              "fer": c[1] / c[0], "ber": c[2] / (c[0] * st["n"]),
+                              "fer": c[1] / c[0], "fer_ci95": [lo, hi], "ber": c[2] / (c[0] * st["n"]),
                               "osd_frames": int(c[4]), "nms_fer": 1 - c[6] / c[0],
-                              "avg_iters": c[5] / c[0], "undetected": int(c[3])})
+                              "avg_iters": c[5] / c[0], "iters_hist": hist.cpu().tolist()[1:],
+                              "undetected": int(c[3])})
             edge_updates += int(st["ctr_local"][pi][5]) * P_AUTOS * E
     frames_per_step = F * len(CODES)
     ms = elapsed / args.steps * 1e3
