@@ -10,6 +10,7 @@ namespace bchlib {
 struct OsdArgs {
   int n, k, M;
   const uint4 *rows;  // [M] standard H rows, 4 x u32
+  const uint64_t *cols;  // [n] standard H column masks over the M rows
   const float *llr;
   int ld;
   const uint32_t *list;

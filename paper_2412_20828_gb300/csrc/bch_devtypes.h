@@ -26,6 +26,7 @@ struct DevCode {
   const uint16_t *codes;          // column codes, group order
   const uint32_t *rowmask;        // [rows][4] bit-packed rows (syndrome test)
   const uint64_t *par;            // [k] parity words (systematic encoder)
+  const uint64_t *colmask;        // [n] column masks over the rows (rows <= 64, else 0)
 };
 
 // Argument block of the enhanced / plain min-sum kernels.

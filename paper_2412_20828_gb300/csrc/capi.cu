@@ -160,11 +160,12 @@ bch_status upload_code(bch_code *c) {
   if (codes.size() % 2) codes.push_back(0);
   dc.edges = edges;
   dc.max_w = maxw;
-  // device blob: codes | rowmask | par | descriptor
+  // device blob: codes | rowmask | par | colmask | descriptor
   const size_t off_codes = 0;
   const size_t off_mask = align256(off_codes + codes.size() * 2);
   const size_t off_par = align256(off_mask + size_t(R) * 16);
-  const size_t off_desc = align256(off_par + size_t(k) * 8);
+  const size_t off_cols = align256(off_par + size_t(k) * 8);
+  const size_t off_desc = align256(off_cols + size_t(n) * 8);
   const size_t total = align256(off_desc + sizeof(DevCode));
   std::vector<unsigned char> host(total, 0);
   std::memcpy(host.data() + off_codes, codes.data(), codes.size() * 2);
@@ -177,12 +178,21 @@ bch_status upload_code(bch_code *c) {
     std::memcpy(host.data() + off_mask + size_t(r) * 16, w4, 16);
   }
   std::memcpy(host.data() + off_par, c->alg.par.data(), size_t(k) * 8);
+  if (R <= 64) {  // column masks: bit r of column u = H[r][u] (the OSD elimination)
+    for (int u = 0; u < n; u++) {
+      uint64_t col = 0;
+      for (int r = 0; r < R; r++)
+        if (c->rows[r].get(u)) col |= 1ull << r;
+      std::memcpy(host.data() + off_cols + size_t(u) * 8, &col, 8);
+    }
+  }
   void *blob = nullptr;
   if (cudaMalloc(&blob, total) != cudaSuccess) return fail(BCH_ENOMEM, "cudaMalloc for the code");
   unsigned char *b = static_cast<unsigned char *>(blob);
   dc.codes = reinterpret_cast<const uint16_t *>(b + off_codes);
   dc.rowmask = reinterpret_cast<const uint32_t *>(b + off_mask);
   dc.par = reinterpret_cast<const uint64_t *>(b + off_par);
+  dc.colmask = reinterpret_cast<const uint64_t *>(b + off_cols);
   std::memcpy(host.data() + off_desc, &dc, sizeof(DevCode));
   cudaError_t e = cudaMemcpy(blob, host.data(), total, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -492,6 +502,7 @@ static bch_status run_osd(const bch_code *std_code, int order, const float *llr,
   a.k = std_code->alg.k;
   a.M = M;
   a.rows = reinterpret_cast<const uint4 *>(std_code->dc.rowmask);
+  a.cols = std_code->dc.colmask;
   a.llr = llr;
   a.ld = ld;
   a.list = list;

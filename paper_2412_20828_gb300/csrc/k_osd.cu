@@ -4,14 +4,13 @@
 // One warp decodes one failed frame:
 //  * reliabilities |L| (FP32) are ranked by counting against 64-bit keys
 //    (|L| bits, index) -- a total order equal to a stable ascending sort;
-//  * Gaussian elimination over GF(2) runs on the standard H in its original column
-//    order, visiting columns from least to most reliable: lane l holds rows l and
-//    l + 32 as 128-bit words, the pivot row is found by ballot and broadcast by
-//    shuffles;
+//  * Gauss-Jordan elimination over GF(2) on the standard H visits columns from least
+//    to most reliable in column-major form (lane l holds the row masks of columns
+//    l + 32 q), one shuffle and a few xors per pivot;
 //  * with the reduced rows, the disagreement pattern of a test pattern e on the
 //    most reliable basis is D(e) = D0 xor (xor of the basis columns in e) restricted
 //    to the n-k pivot positions, so a candidate costs a few XORs plus a weighted
-//    popcount done with eight 256-entry tables of pivot weights;
+//    popcount done with 16-entry tables of pivot weights (one per 4 pivot rows);
 //  * scores are exact 64-bit integers (weights floor(|L| 2^24)), and the warp keeps
 //    the lexicographic minimum of (score, enumeration index): the result equals a
 //    sequential scan that keeps the first minimum.
@@ -34,7 +33,7 @@ __global__ void __launch_bounds__(32 * kOsdWarps) osd_kernel(const OsdArgs a) {
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
     const int f = int(a.list[item]);
-    osd_one_frame(S, a.n, a.k, a.M, a.rows, a.llr + size_t(f) * a.ld, a.order, a.hard + size_t(f) * W64,
+    osd_one_frame(S, a.n, a.k, a.M, a.cols, a.llr + size_t(f) * a.ld, a.order, a.hard + size_t(f) * W64,
                   a.flags ? a.flags + f : nullptr);
   }
 }

@@ -113,6 +113,7 @@ extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_
   o.k = std_code->alg.k;
   o.M = M;
   o.rows = reinterpret_cast<const uint4 *>(std_code->dc.rowmask);
+  o.cols = std_code->dc.colmask;
   o.llr = llr;
   o.ld = ld;
   o.list = list;

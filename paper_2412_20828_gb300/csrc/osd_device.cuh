@@ -4,10 +4,11 @@
 // One warp decodes one failed frame:
 //  * reliabilities |L| (FP32) are ranked by counting against 64-bit keys
 //    (|L| bits, index) -- a total order equal to a stable ascending sort;
-//  * Gaussian elimination over GF(2) runs on the standard H in its original column
-//    order, visiting columns from least to most reliable: lane l holds rows l and
-//    l + 32 as 128-bit words, the pivot row is found by ballot and broadcast by
-//    shuffles;
+//  * Gauss-Jordan elimination over GF(2) on the standard H visits columns from least
+//    to most reliable in column-major form: lane l holds the row masks of columns l,
+//    l + 32, l + 64, l + 96; a pivot step fetches the column's mask by one shuffle,
+//    takes its lowest unpivoted row and xors the column (minus that row) into every
+//    column having the row;
 //  * with the reduced rows, the disagreement pattern of a test pattern e on the
 //    most reliable basis is D(e) = D0 xor (xor of the basis columns in e) restricted
 //    to the n-k pivot positions, so a candidate costs a few XORs plus a weighted
@@ -32,25 +33,15 @@ struct OsdSmem {
   unsigned long long wm[128];  // weights of the MRB positions, by basis index
   unsigned long long wp[64];   // weights of the pivot positions, by row
   unsigned long long tab[16][16];  // weighted popcount of each 4-row chunk
+  unsigned long long colm[128];    // reduced column masks, by original index
   uint8_t perm[128];           // sorted position -> original index
   uint8_t mrb[128];            // basis index -> original index
   uint8_t ispiv[128];          // by original index
+  uint8_t pivcol[64];          // pivot column of each row
 };
 
-__device__ __forceinline__ bool bit128(uint4 r, uint32_t c) {
-  const uint32_t w = c < 32 ? r.x : (c < 64 ? r.y : (c < 96 ? r.z : r.w));
-  return (w >> (c & 31)) & 1u;
-}
 __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
   return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
-}
-__device__ __forceinline__ uint4 and4(uint4 a, uint4 b) {
-  return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
-}
-__device__ __forceinline__ uint32_t parity4(uint4 a) { return __popc(a.x ^ a.y ^ a.z ^ a.w) & 1u; }
-__device__ __forceinline__ uint4 shfl4(uint4 v, int src) {
-  return make_uint4(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src),
-                    __shfl_sync(kFull, v.z, src), __shfl_sync(kFull, v.w, src));
 }
 
 __device__ __forceinline__ unsigned long long wsum(const OsdSmem &S, unsigned long long D, int nch) {
@@ -73,33 +64,54 @@ __device__ __forceinline__ void consider(Best &b, unsigned long long s, uint32_t
   }
 }
 
+// Mask of the M <= 64 rows: 32 bits when M <= 32.
+template <typename MT>
+__device__ __forceinline__ MT shfl_mask(MT v, int src) {
+  if constexpr (sizeof(MT) == 4) {
+    return __shfl_sync(kFull, v, src);
+  } else {
+    const uint32_t lo = __shfl_sync(kFull, uint32_t(v), src);
+    const uint32_t hi = __shfl_sync(kFull, uint32_t(v >> 32), src);
+    return (MT(hi) << 32) | lo;
+  }
+}
+template <typename MT>
+__device__ __forceinline__ int ffs_mask(MT v) {
+  if constexpr (sizeof(MT) == 4) return __ffs(v) - 1;
+  else return __ffsll((long long)v) - 1;
+}
+
 // Order-p OSD of one frame by one warp (all 32 lanes call it with the same
-// arguments).  L: the frame's FP32 channel LLRs; rows: the M standard-H rows;
-// hard: the frame's ceil(n/64) output words; flag: its flag byte (nullable).
-__device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, const uint4 *rows,
-                                              const float *L, int order, uint64_t *hard,
-                                              uint8_t *flag) {
+// arguments).  L: the frame's FP32 channel LLRs; cols: the n column masks of the
+// standard H over its M rows; hard: the frame's ceil(n/64) output words; flag: its
+// flag byte (nullable).  MT: the row-mask type (uint32_t when M <= 32).
+//
+// The elimination is column-major: lane l keeps the masks of columns l, l + 32, l + 64
+// and l + 96.  Pivoting on column c (least reliable first) takes its current mask v,
+// the lowest not-yet-pivoted row r in v, and adds row r to every other row of v -- in
+// column form, every column whose mask has bit r gets v without bit r xored in
+// (Gauss-Jordan over all rows, the same steps as a row-major elimination).
+template <typename MT>
+__device__ __forceinline__ void osd_one_frame_t(OsdSmem &S, int n, int K, int M, const uint64_t *cols,
+                                                const float *L, int order, uint64_t *hard,
+                                                uint8_t *flag) {
   const int lane = int(lane_id());
-  // ---- reliabilities, hard decision, weights
-  float lv[4];
-  unsigned long long wv[4];
+  // ---- reliabilities, hard decision, sort keys
   uint4 h = make_uint4(0, 0, 0, 0);
+  MT colm[4];
 #pragma unroll
   for (int r = 0; r < 4; r++) {
     const int i = lane + 32 * r;
-    lv[r] = i < n ? L[i] : 0.0f;
-    const float al = fabsf(lv[r]);
-    const float fw = fminf(floorf(al * 16777216.0f), 1099511627776.0f);
-    wv[r] = __float2ull_rz(fw);
-    const unsigned hb = __ballot_sync(kFull, i < n && lv[r] < 0.0f);
+    const float lv = i < n ? L[i] : 0.0f;
+    const float al = fabsf(lv);
+    const unsigned hb = __ballot_sync(kFull, i < n && lv < 0.0f);
     if (r == 0) h.x = hb;
     if (r == 1) h.y = hb;
     if (r == 2) h.z = hb;
     if (r == 3) h.w = hb;
-    if (i < 128)
-      S.key[i] = i < n ? ((unsigned long long)__float_as_uint(al) << 7) | unsigned(i)
-                       : ~0ull;
-    if (i < 128) S.ispiv[i] = 0;
+    S.key[i] = i < n ? ((unsigned long long)__float_as_uint(al) << 7) | unsigned(i) : ~0ull;
+    S.ispiv[i] = 0;
+    colm[r] = i < n ? MT(__ldg(cols + i)) : MT(0);
   }
   __syncwarp();
   // rank by counting (keys are distinct)
@@ -114,34 +126,46 @@ __device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, c
     }
   }
   __syncwarp();
-  // ---- elimination in reliability order
-  uint4 row0 = make_uint4(0, 0, 0, 0), row1 = make_uint4(0, 0, 0, 0);
-  if (lane < M) row0 = rows[lane];
-  if (lane + 32 < M) row1 = rows[lane + 32];
-  bool piv0 = lane >= M, piv1 = lane + 32 >= M;
-  int pc0 = 0, pc1 = 0;
+  // ---- elimination in reliability order (column-major)
+  MT pivoted = 0;
   int npiv = 0;
   for (int q = 0; q < n && npiv < M; q++) {
-    const uint32_t c = S.perm[q];
-    const unsigned m0 = __ballot_sync(kFull, !piv0 && bit128(row0, c));
-    const unsigned m1 = __ballot_sync(kFull, !piv1 && bit128(row1, c));
-    if ((m0 | m1) == 0) continue;
-    const int pr = m0 ? (__ffs(m0) - 1) : (32 + __ffs(m1) - 1);
-    const int src = pr & 31;
-    const uint4 pv = shfl4(pr < 32 ? row0 : row1, src);
-    if (bit128(row0, c) && lane != pr) row0 = xor4(row0, pv);
-    if (bit128(row1, c) && lane + 32 != pr) row1 = xor4(row1, pv);
-    if (lane == pr) {
-      piv0 = true;
-      pc0 = int(c);
+    const int c = S.perm[q];
+    const int cw = c >> 5;
+    const MT mine = cw == 0 ? colm[0] : cw == 1 ? colm[1] : cw == 2 ? colm[2] : colm[3];
+    const MT v = shfl_mask(mine, c & 31);
+    const MT cand = v & ~pivoted;
+    if (cand == 0) continue;
+    const int r = ffs_mask(cand);
+    const MT rbit = MT(1) << r;
+    const MT vm = v & ~rbit;
+    pivoted |= rbit;
+    if (lane == 0) {
+      S.pivcol[r] = uint8_t(c);
+      S.ispiv[c] = 1;
     }
-    if (lane + 32 == pr) {
-      piv1 = true;
-      pc1 = int(c);
-    }
-    if (lane == 0) S.ispiv[c] = 1;
+#pragma unroll
+    for (int w = 0; w < 4; w++)
+      if (colm[w] & rbit) colm[w] ^= vm;
     npiv++;
   }
+  // reduced columns by original index
+#pragma unroll
+  for (int w = 0; w < 4; w++) {
+    const int i = lane + 32 * w;
+    if (i < n) S.colm[i] = (unsigned long long)colm[w];
+  }
+  // D0: disagreement of the re-encoded hard decision on the pivot rows = xor of the
+  // columns the hard decision has set
+  MT d0 = 0;
+  {
+    const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+    for (int w = 0; w < 4; w++)
+      if ((hw[w] >> lane) & 1u) d0 ^= colm[w];
+    for (int off = 16; off > 0; off >>= 1) d0 ^= shfl_mask(d0, (lane ^ off));
+  }
+  const unsigned long long D0 = (unsigned long long)d0;
   __syncwarp();
   // ---- most reliable basis in sorted order
   int kk = 0;
@@ -159,24 +183,13 @@ __device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, c
     const float al = fabsf(L[ci]);
     S.wm[a2] = __float2ull_rz(fminf(floorf(al * 16777216.0f), 1099511627776.0f));
   }
-  {
-    const float al0 = lane < M ? fabsf(L[pc0]) : 0.f;
-    const float al1 = lane + 32 < M ? fabsf(L[pc1]) : 0.f;
-    S.wp[lane] = lane < M ? __float2ull_rz(fminf(floorf(al0 * 16777216.0f), 1099511627776.0f)) : 0ull;
-    S.wp[lane + 32] =
-        lane + 32 < M ? __float2ull_rz(fminf(floorf(al1 * 16777216.0f), 1099511627776.0f)) : 0ull;
+  // weights of the pivot positions, by row
+  for (int r = lane; r < 64; r += 32) {
+    const float al = r < M ? fabsf(L[S.pivcol[r]]) : 0.f;
+    S.wp[r] = r < M ? __float2ull_rz(fminf(floorf(al * 16777216.0f), 1099511627776.0f)) : 0ull;
   }
   // basis columns restricted to the pivot rows
-  for (int a2 = 0; a2 < K; a2++) {
-    const uint32_t c = S.mrb[a2];
-    const unsigned b0 = __ballot_sync(kFull, lane < M && bit128(row0, c));
-    const unsigned b1 = __ballot_sync(kFull, lane + 32 < M && bit128(row1, c));
-    if (lane == 0) S.colbits[a2] = (unsigned long long)b0 | ((unsigned long long)b1 << 32);
-  }
-  // D0: disagreement of the re-encoded hard decision on the pivot positions
-  const unsigned d0a = __ballot_sync(kFull, lane < M && parity4(and4(row0, h)));
-  const unsigned d0b = __ballot_sync(kFull, lane + 32 < M && parity4(and4(row1, h)));
-  const unsigned long long D0 = (unsigned long long)d0a | ((unsigned long long)d0b << 32);
+  for (int a2 = lane; a2 < K; a2 += 32) S.colbits[a2] = S.colm[S.mrb[a2]];
   __syncwarp();
   const int nch = (M + 3) / 4;
   if (lane < nch) S.tab[lane][0] = 0ull;
@@ -240,8 +253,8 @@ __device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, c
     else if (c < 96) v.z ^= m;
     else v.w ^= m;
   };
-  if (lane < M && ((D >> lane) & 1ull)) setb(flip, pc0);
-  if (lane + 32 < M && ((D >> (lane + 32)) & 1ull)) setb(flip, pc1);
+  if (lane < M && ((D >> lane) & 1ull)) setb(flip, S.pivcol[lane]);
+  if (lane + 32 < M && ((D >> (lane + 32)) & 1ull)) setb(flip, S.pivcol[lane + 32]);
   for (int off = 16; off > 0; off >>= 1) {
     flip.x ^= __shfl_xor_sync(kFull, flip.x, off);
     flip.y ^= __shfl_xor_sync(kFull, flip.y, off);
@@ -258,6 +271,15 @@ __device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, c
     if (flag) *flag |= uint8_t(kFlagOsd);
   }
   __syncwarp();
+}
+
+// Dispatch on the row count: 32-bit row masks when M <= 32.
+__device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, const uint64_t *cols,
+                                              const float *L, int order, uint64_t *hard, uint8_t *flag) {
+  if (M <= 32)
+    osd_one_frame_t<uint32_t>(S, n, K, M, cols, L, order, hard, flag);
+  else
+    osd_one_frame_t<unsigned long long>(S, n, K, M, cols, L, order, hard, flag);
 }
 
 }  // namespace bchlib

@@ -46,7 +46,7 @@ constexpr int kSrvMaxCodes = 8;
 struct SrvCode {
   DevCode dc;
   const GroupDesc *grp;  // [kMaxGroups] in device memory
-  const uint4 *std_rows;
+  const uint64_t *std_cols;  // standard H column masks (OSD)
   int M, has_osd, wb, ord;  // ord: order of 2 mod n (Frobenius exponents)
 };
 
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(32) serve_kernel(const SrvArgs a) {
         const int l = __ffs(fail) - 1;
         fail &= fail - 1;
         const int f = start + l;
-        osd_one_frame(S, cd.dc.n, cd.dc.k, cd.M, cd.std_rows, sl.llr + size_t(f) * sl.ld, a.order,
+        osd_one_frame(S, cd.dc.n, cd.dc.k, cd.M, cd.std_cols, sl.llr + size_t(f) * sl.ld, a.order,
                       sl.hard + size_t(f) * W64, sl.flags + f);
       }
     }
@@ -591,7 +591,7 @@ bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
       grp[size_t(c) * kMaxGroups + g] = d;
     }
     sc_.grp = s->grp_dev + size_t(c) * kMaxGroups;
-    sc_.std_rows = sc ? reinterpret_cast<const uint4 *>(sc->dc.rowmask) : nullptr;
+    sc_.std_cols = sc ? sc->dc.colmask : nullptr;
     sc_.M = sc ? sc->alg.n - sc->alg.k : 0;
     sc_.has_osd = sc ? 1 : 0;
     sc_.ord = 1;
