@@ -112,10 +112,10 @@ bch_status bch_build_pcm_host(int n, int k, bch_pcm_kind kind, int m_rows, uint6
  * automorphisms runs: "jit" -- the kernel compiled at run time (NVRTC) for this code's
  * Tanner graph, rows as straight-line code on registers -- or "generic: <reason>" --
  * the precompiled kernel that reads the rows from shared memory.  The environment
- * variable BCHDEC_NMS_KERNEL=generic|jit|auto selects (default auto: jit for n <= 63
- * when it compiles, generic for n = 127, where the specialised kernel is about 1.8x
- * faster but takes about two minutes to compile).  The first call for a code compiles
- * (a few seconds for n <= 63) and caches the kernel in the process and on disk
+ * variable BCHDEC_NMS_KERNEL=generic|jit|auto selects (default auto: jit when it
+ * compiles, else generic; for n = 127 the specialised kernel is about 1.8x faster than
+ * the precompiled one).  The first call for a code compiles (a few seconds for n <= 63,
+ * 30-90 s for n = 127) and caches the kernel in the process and on disk
  * (BCHDEC_JIT_CACHE_DIR, default $XDG_CACHE_HOME/bchdec or $HOME/.cache/bchdec; "off"
  * disables it).  Tuning knobs of the specialised kernel, read when its source is
  * generated: BCHDEC_JIT_TPB (block size for n <= 63), BCHDEC_JIT_MIN_BLOCKS (register

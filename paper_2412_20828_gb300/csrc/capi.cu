@@ -317,8 +317,6 @@ bch_status bch_nms_kernel_info(const bch_code *code, int msg, int n_autos, char 
     info = "generic: plain decoder";
   } else if (mode == 1) {
     info = "generic: selected by BCHDEC_NMS_KERNEL";
-  } else if (mode == 0 && code->alg.n > 63) {
-    info = "generic: n = 127 (the specialised kernel is opt-in: BCHDEC_NMS_KERNEL=jit)";
   } else {
     std::string err;
     cudaKernel_t k = jit_kernel(code, msg, &err);
@@ -445,9 +443,10 @@ static cudaError_t launch_jit(cudaKernel_t k, const bch_code *code, const NmsArg
 static cudaError_t launch_nms_code(const bch_code *code, const NmsArgs &a, cudaStream_t st,
                                    std::string *why) {
   const int mode = kernel_mode();
-  // auto: the specialised kernel for n <= 63; for n = 127 its compile time (tens of
-  // seconds) and register spills make the precompiled kernel the default
-  if (a.P > 0 && (mode == 2 || (mode == 0 && code->alg.n <= 63))) {
+  // auto and jit: the specialised kernel (for n = 127 it spills but still runs 1.8x
+  // faster than the precompiled one; its first compile takes tens of seconds and is
+  // cached on disk); auto falls back to the precompiled kernel if it does not compile
+  if (a.P > 0 && mode != 1) {
     std::string err;
     cudaKernel_t k = jit_kernel(code, a.msg, &err);
     if (k) return launch_jit(k, code, a, st);

@@ -230,9 +230,10 @@ std::string jit_source(const bch_code *c, int msg) {
   // rows, grouped by weight like the device image
   const int fma_pct = jit_fma_percent();
   int fma_acc = 0;
-  // n = 127: a compiler fence after each row keeps the scheduler from overlapping the
-  // shared-memory row sums of many rows while 127 z values are live (fewer spills)
-  const bool fence = env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, n > 63 ? 1 : 0) == 1;
+  // BCHDEC_JIT_ROW_FENCE=1: a compiler fence after each row keeps the scheduler from
+  // overlapping the shared-memory row sums of many rows (n = 127: 0.55 KB of spills
+  // instead of 2.5 KB, but measured 4% slower, so off by default)
+  const bool fence = env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, 0) == 1;
   for (const Row &row : c->rows) {
     std::vector<int> cols;
     for (int u = 0; u < n; u++)

@@ -45,7 +45,7 @@ def paper_block(n: int, m: int, frames: int, frame0: int, seed: int) -> np.ndarr
     return out
 
 
-def run(frames=1_000_000, alphas=(0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9), chunk=1 << 19,
+def run(frames=1_000_000, alphas=(0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95, 1.0), chunk=1 << 19,
         seed=0x2412, log=sys.stderr):
     import torch
     from . import bchdec as B

@@ -301,16 +301,17 @@ def test_count_errors(torch_cuda):
 
 
 # ------------------------------------------------------------------ kernel variants
+@pytest.mark.parametrize("nk", [(63, 36), (127, 64)])
 @pytest.mark.parametrize("msg", [B.MSG_FP32, B.MSG_INT8])
-def test_jit_and_generic_kernels_agree(torch_cuda, msg, monkeypatch):
+def test_jit_and_generic_kernels_agree(torch_cuda, msg, nk, monkeypatch):
     # the run-time specialised kernel and the precompiled kernel compute the same
     # decoder: INT8 sums are exact integers (bit-exact), FP32 differs only in the
     # association of the c2v sums
-    n, k = 63, 36
+    n, k = nk
     c = code(n, k)
     assert c.kernel_info(msg) == "jit"
     F = 2000
-    cw, llr = frames(n, k, F, 2.0, 1234, ld=64)
+    cw, llr = frames(n, k, F, 2.0 if n == 63 else 3.0, 1234, ld=64 if n == 63 else 128)
     autos = O.draw_autos(n, 3, 77, 0, F)
     a = run_nms(torch_cuda, c, llr, autos, 12, 0.78, msg=msg)
     monkeypatch.setenv("BCHDEC_NMS_KERNEL", "generic")
