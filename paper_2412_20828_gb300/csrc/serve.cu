@@ -3,15 +3,17 @@
 // hybrid decoder (enhanced NMS, OSD on the frames it fails) while other requests are
 // already on the GPU.
 //
-// Device side: one warp per block; a warp claims up to 32 frames of the oldest
-// admitted request that still has unclaimed frames (atomic claim counter per slot),
-// decodes them one frame per lane (enhanced NMS, rows of any of the server's codes
-// read from global memory), runs OSD warp-cooperatively on the frames whose syndrome
-// stayed nonzero (in the same shared-memory region), then adds the frames to the
-// slot's done counter; the warp that completes a request posts a completion record
-// to a ring in host-mapped memory.  Every wait is bounded: idle warps sleep and the
-// kernel exits after `idle_exit_us` without work (the host relaunches it), and a stop
-// flag ends it at the next chunk boundary.
+// Device side: one warp per block; each lane decodes one frame at a time and, when
+// its frame stops, takes the next unclaimed frame of the warp's code (requests of a
+// code are published to that code's ring; claims are generation-checked CAS on a
+// per-request counter and may span requests), so lanes never wait for a chunk's
+// slowest frame.  A warp binds to one code while any lane has a frame and picks a
+// code with published work when all its lanes are idle.  Frames whose syndrome stays
+// nonzero get OSD from the whole warp; every finished frame is added to its request's
+// done counter and the frame that completes a request posts a completion record to a
+// ring in host-mapped memory.  Every wait is bounded: idle warps sleep and the kernel
+// exits after `idle_exit_us` without work (the host relaunches it), and a stop flag
+// ends it at the next iteration.
 //
 // The automorphisms of a frame are drawn inside the kernel from (seed, frame index):
 // admission launches no kernel, because the persistent kernel holds every SM's shared
@@ -74,18 +76,19 @@ struct SrvComp {
 // Host-mapped control block (written by the host: sub_ring / sub_tail / stop;
 // written by the device: comp / running).
 struct SrvShared {
-  volatile unsigned sub_tail;
+  volatile unsigned sub_tail[kSrvMaxCodes];  // per code: requests published so far
   volatile unsigned stop;
   volatile unsigned running;
-  volatile unsigned live_blocks;
-  unsigned pad[4];
+  unsigned pad[6];
 };
 
+static_assert(sizeof(SrvShared) <= 64, "the submission rings start at byte 64");
+
 struct SrvDev {
-  unsigned head;
+  unsigned head[kSrvMaxCodes];  // per code: first ring entry not yet fully claimed
   unsigned comp_tail;
   unsigned live;
-  unsigned pad;
+  unsigned pad[6];
 };
 
 struct SrvArgs {
@@ -94,7 +97,7 @@ struct SrvArgs {
   int n_codes;
   SrvSlot *slots;
   SrvShared *sh;
-  unsigned *sub_ring;  // host-mapped [ring]
+  unsigned *sub_ring;  // host-mapped [kSrvMaxCodes][ring]: slot | generation << 16
   SrvComp *comp;       // host-mapped [ring]
   SrvDev *dv;
   int ring;
@@ -118,148 +121,199 @@ __device__ __forceinline__ SrvSlot load_slot(const SrvSlot *p) {
   return s;
 }
 
-// Enhanced NMS of up to 32 frames (one per lane) of one request, all iterations.
+// P automorphism copies of one enhanced-NMS iteration for this lane's frame (rows of
+// the warp's code read from global memory; columns of stride 32 in shared memory).
 template <int WB>
-__device__ __noinline__ void srv_nms_chunk(const SrvArgs &a, const SrvCode &cd, const SrvSlot &sl, int f0,
-                                           int cnt, float *y, float *acc, uint32_t *ctx) {
-  const int lane = int(lane_id());
-  const int n = cd.dc.n;
-  const uint32_t m = uint32_t(cd.dc.m);
-  const bool act0 = lane < cnt;
-  const int f = f0 + lane;
+__device__ __noinline__ void srv_copies(const SrvCode &cd, int P, float *y, float *acc, const uint32_t *ctx,
+                                        float alpha) {
   SmemTables tb;
   tb.codes = const_cast<uint16_t *>(cd.dc.codes);
   tb.grp = const_cast<GroupDesc *>(cd.grp);
   tb.rowmask = reinterpret_cast<uint4 *>(const_cast<uint32_t *>(cd.dc.rowmask));
   tb.alpha = nullptr;
   tb.state = nullptr;
-  if (act0) {
-    const float *src = sl.llr + size_t(f) * sl.ld;
-    for (int i = 0; i < n; i++) {
-      y[i * 32] = src[i] + 0.0f;
-      acc[i * 32] = 0.0f;
+  const uint32_t n = uint32_t(cd.dc.n), m = uint32_t(cd.dc.m);
+  for (int p = 0; p < P; p++) {
+    const uint32_t cx = ctx[p * 32];
+    enh_copy<kFP32, WB>(tb, cd.dc.n_groups, n, m, y, acc, cx & 0xffu, cx >> 8, 32u, alpha);
+  }
+}
+
+// Claims up to `want` frames of code c for a warp (lane 0 only): walks the code's
+// submission ring from its head, taking frames from each request by a
+// generation-checked CAS on the request's claim word and moving the head past
+// requests that are fully claimed (or replaced).  Bounded attempts.  Writes the
+// segments (slot, first frame, count) to seg[0..], seg[32..], seg[64..].
+__device__ int srv_claim(const SrvArgs &a, int c, int want, int *seg) {
+  int nseg = 0;
+  unsigned *headp = a.dv->head + c;
+  for (int tries = 0; tries < 8 && want > 0 && nseg < 32; tries++) {
+    const unsigned h = *reinterpret_cast<volatile unsigned *>(headp);
+    const unsigned tail = a.sh->sub_tail[c];
+    if (h == tail) break;
+    __threadfence_system();
+    const unsigned e =
+        *reinterpret_cast<volatile unsigned *>(&a.sub_ring[size_t(c) * a.ring + h % unsigned(a.ring)]);
+    const int sidx = int(e & 0xffffu);
+    const unsigned gen = e >> 16;
+    SrvSlot *sp = a.slots + sidx;
+    const unsigned long long cl = *reinterpret_cast<volatile unsigned long long *>(&sp->claim);
+    const unsigned next = unsigned(cl);
+    const int F = *reinterpret_cast<volatile int *>(&sp->F);
+    if (((cl >> 32) & 0xffffu) != gen || int(next) >= F) {
+      atomicCAS(headp, h, h + 1);  // fully claimed or replaced: move on
+      continue;
     }
-    uint32_t va[9];
-    draw_frame_autos(n, cd.ord, a.P, sl.seed, sl.frame0 + uint64_t(f), va);
-    for (int p = 0; p < a.P; p++) {
-      const uint32_t v = va[p];
-      const uint32_t s = v & 0xffu, j = v >> 8;
-      const uint32_t rs = j ? (((s >> j) | (s << (m - j))) & uint32_t(n)) : s;
-      ctx[p * 32] = j | ((rs ? uint32_t(n) - rs : 0u) << 8);
+    const int take = min(want, F - int(next));
+    if (atomicCAS(&sp->claim, cl, cl + (unsigned long long)take) == cl) {
+      seg[nseg] = sidx;
+      seg[32 + nseg] = int(next);
+      seg[64 + nseg] = take;
+      nseg++;
+      want -= take;
+      if (int(next) + take >= F) atomicCAS(headp, h, h + 1);
     }
   }
-  bool act = act0;
-  int t = 0;
-  uint32_t cb[4] = {0, 0, 0, 0};
-  uint32_t nz = 1;
+  return nseg;
+}
+
+// The persistent serving kernel.  One warp per block; each lane decodes one frame at a
+// time and, when its frame stops, takes the next frame of the same code (across
+// request boundaries), so early stopping turns into throughput as in the batch
+// kernels.  The warp binds to one code while any lane has a frame and picks a code
+// with published work when all its lanes are idle.  Frames whose syndrome stays
+// nonzero get order-p OSD from the whole warp before they are counted done.
+__global__ void __launch_bounds__(32) serve_kernel(const SrvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *acc = reinterpret_cast<float *>(smem);
+  float *y = acc + 128 * 32;
+  OsdSmem &S = *reinterpret_cast<OsdSmem *>(y + 128 * 32);
+  uint32_t *ctx = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(&S) + sizeof(OsdSmem));
+  int *seg = reinterpret_cast<int *>(ctx + 9 * 32);
+  const int lane = int(lane_id());
+  if (lane == 0) atomicAdd(&a.dv->live, 1u);
+  unsigned long long idle_since = globaltimer();
+  unsigned sleep_ns = 64;
+  int wc = -1;                    // the code this warp decodes (warp-uniform)
+  int slot = -1, f = -1, t = 0;   // this lane's frame
   const float invP = 1.0f / float(a.P);
-  while (__any_sync(kFull, act)) {
-    if (act) {
-      const float alpha = __ldg(a.alpha + t);
-      for (int p = 0; p < a.P; p++) {
-        const uint32_t cx = ctx[p * 32];
-        enh_copy<kFP32, WB>(tb, cd.dc.n_groups, uint32_t(n), m, y, acc, cx & 0xffu, cx >> 8, 32u, alpha);
-      }
-      cb[0] = cb[1] = cb[2] = cb[3] = 0;
-#pragma unroll
-      for (int i = 0; i < 128; i++) {
-        if (i < n) {
-          const float yn = __fmaf_rn(acc[i * 32], invP, y[i * 32]);
-          y[i * 32] = yn;
-          acc[i * 32] = 0.0f;
-          cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
+  for (;;) {
+    if (a.sh->stop) break;
+    // ---- an idle warp binds to a code with published work
+    if (!__any_sync(kFull, f >= 0)) {
+      int pick = -1;
+      if (lane == 0) {
+        for (int q = 0; q < a.n_codes; q++) {
+          const int c = (wc + 1 + q + int(blockIdx.x)) % a.n_codes;
+          if (*reinterpret_cast<volatile unsigned *>(&a.dv->head[c]) != a.sh->sub_tail[c]) {
+            pick = c;
+            break;
+          }
         }
       }
+      pick = __shfl_sync(kFull, pick, 0);
+      if (pick < 0) {
+        if (globaltimer() - idle_since > a.idle_ns) break;
+        __nanosleep(sleep_ns);
+        sleep_ns = sleep_ns < 20000 ? sleep_ns * 2 : sleep_ns;
+        continue;
+      }
+      wc = pick;
+    }
+    const SrvCode &cd = a.codes[wc];  // device memory
+    const int n = cd.dc.n;
+    // ---- idle lanes take the next frames of the code
+    const unsigned need = __ballot_sync(kFull, f < 0);
+    if (need) {
+      int nseg = 0;
+      if (lane == 0) nseg = srv_claim(a, wc, __popc(need), seg);
+      nseg = __shfl_sync(kFull, nseg, 0);
+      __syncwarp();
+      if (f < 0 && nseg > 0) {
+        int r = __popc(need & ((1u << lane) - 1u));
+        for (int q = 0; q < nseg; q++) {
+          const int cnt = seg[64 + q];
+          if (r < cnt) {
+            slot = seg[q];
+            f = seg[32 + q] + r;
+            break;
+          }
+          r -= cnt;
+        }
+        if (f >= 0) {
+          // the host rewrites a slot between requests: read the descriptor past L1
+          const SrvSlot sl = load_slot(a.slots + slot);
+          const float *src = sl.llr + size_t(f) * sl.ld;
+          for (int i = 0; i < n; i++) {
+            y[i * 32 + lane] = src[i] + 0.0f;  // -0 -> +0
+            acc[i * 32 + lane] = 0.0f;
+          }
+          uint32_t va[9];
+          draw_frame_autos(n, cd.ord, a.P, sl.seed, sl.frame0 + uint64_t(f), va);
+          const uint32_t m = uint32_t(cd.dc.m);
+          for (int p = 0; p < a.P; p++) {
+            const uint32_t sh = va[p] & 0xffu, j = va[p] >> 8;
+            // pi^-1(u) = rotr_m(u, j) + s' with s' = -rotr_m(s, j) mod n
+            const uint32_t rs = j ? (((sh >> j) | (sh << (m - j))) & uint32_t(n)) : sh;
+            ctx[p * 32 + lane] = j | ((rs ? uint32_t(n) - rs : 0u) << 8);
+          }
+          t = 0;
+        }
+      }
+      __syncwarp();
+    }
+    const bool active = f >= 0;
+    if (!__any_sync(kFull, active)) continue;
+    sleep_ns = 64;
+    idle_since = globaltimer();
+    // ---- one iteration for the active lanes
+    bool done = false;
+    uint32_t nz = 0;
+    uint32_t cb[4] = {0u, 0u, 0u, 0u};
+    if (active) {
+      const float alpha = __ldg(a.alpha + t);
+      switch (cd.wb) {
+        case 8: srv_copies<8>(cd, a.P, y + lane, acc + lane, ctx + lane, alpha); break;
+        case 16: srv_copies<16>(cd, a.P, y + lane, acc + lane, ctx + lane, alpha); break;
+        case 24: srv_copies<24>(cd, a.P, y + lane, acc + lane, ctx + lane, alpha); break;
+        case 32: srv_copies<32>(cd, a.P, y + lane, acc + lane, ctx + lane, alpha); break;
+        default: srv_copies<48>(cd, a.P, y + lane, acc + lane, ctx + lane, alpha); break;
+      }
+      for (int i = 0; i < n; i++) {
+        const float yn = __fmaf_rn(acc[i * 32 + lane], invP, y[i * 32 + lane]);
+        y[i * 32 + lane] = yn;
+        acc[i * 32 + lane] = 0.0f;
+        cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
+      }
       t++;
-      nz = syndrome_nonzero<4>(tb.rowmask, cd.dc.rows, cb);
-      if (t >= a.iters || (a.early_stop && nz == 0)) {
+      nz = syndrome_nonzero<4>(reinterpret_cast<const uint4 *>(cd.dc.rowmask), cd.dc.rows, cb);
+      done = t >= a.iters || (a.early_stop && nz == 0);
+      if (done) {
+        const SrvSlot sl = load_slot(a.slots + slot);
         const int W64 = (n + 63) / 64;
         sl.hard[size_t(f) * W64] = uint64_t(cb[0]) | (uint64_t(cb[1]) << 32);
         if (W64 > 1) sl.hard[size_t(f) * W64 + 1] = uint64_t(cb[2]) | (uint64_t(cb[3]) << 32);
         sl.iters[f] = uint8_t(t);
         sl.flags[f] = nz ? 0 : uint8_t(kFlagConverged);
-        act = false;
       }
     }
-  }
-}
-
-__global__ void __launch_bounds__(32) serve_kernel(const SrvArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float *acc = reinterpret_cast<float *>(smem);
-  float *y = acc + 128 * 32;
-  uint32_t *ctx = reinterpret_cast<uint32_t *>(y + 128 * 32);
-  OsdSmem &S = *reinterpret_cast<OsdSmem *>(smem);  // aliases the NMS columns
-  const int lane = int(lane_id());
-  if (lane == 0) atomicAdd(&a.dv->live, 1u);
-  unsigned long long idle_since = globaltimer();
-  unsigned sleep_ns = 64;
-  for (;;) {
-    if (a.sh->stop) break;
-    int slot = -1, start = 0;
-    if (lane == 0) {
-      const unsigned h = *reinterpret_cast<volatile unsigned *>(&a.dv->head);
-      const unsigned tail = a.sh->sub_tail;
-      if (h != tail) {
-        __threadfence_system();
-        const unsigned e = *reinterpret_cast<volatile unsigned *>(&a.sub_ring[h % unsigned(a.ring)]);
-        const int s = int(e & 0xffffu);
-        const unsigned gen = e >> 16;
-        SrvSlot *sp = a.slots + s;
-        slot = -2;
-        for (int tries = 0; tries < 64; tries++) {  // bounded CAS retries
-          const unsigned long long c = *reinterpret_cast<volatile unsigned long long *>(&sp->claim);
-          const unsigned next = unsigned(c);
-          const int F = *reinterpret_cast<volatile int *>(&sp->F);
-          if (((c >> 32) & 0xffffu) != gen || int(next) >= F) {
-            atomicCAS(&a.dv->head, h, h + 1);  // request fully claimed (or replaced): move on
-            break;
-          }
-          if (atomicCAS(&sp->claim, c, c + 32ull) == c) {
-            slot = s;
-            start = int(next);
-            break;
-          }
-        }
-      }
-    }
-    slot = __shfl_sync(kFull, slot, 0);
-    start = __shfl_sync(kFull, start, 0);
-    if (slot == -2) continue;
-    if (slot < 0) {
-      if (globaltimer() - idle_since > a.idle_ns) break;
-      __nanosleep(sleep_ns);
-      sleep_ns = sleep_ns < 20000 ? sleep_ns * 2 : sleep_ns;
-      continue;
-    }
-    sleep_ns = 64;
-    // the host rewrites a slot between requests: read the descriptor past L1
-    const SrvSlot sl = load_slot(a.slots + slot);  // stable until this chunk is counted done
-    const SrvCode &cd = a.codes[sl.code];  // device memory
-    const int cnt = min(32, sl.F - start);
-    switch (cd.wb) {
-      case 8: srv_nms_chunk<8>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
-      case 16: srv_nms_chunk<16>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
-      case 24: srv_nms_chunk<24>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
-      case 32: srv_nms_chunk<32>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
-      default: srv_nms_chunk<48>(a, cd, sl, start, cnt, y + lane, acc + lane, ctx + lane); break;
-    }
+    // ---- OSD of the frames that stopped with a nonzero syndrome (whole warp)
+    const unsigned fail = __ballot_sync(kFull, done && nz != 0 && cd.has_osd);
     __syncwarp();
-    if (cd.has_osd) {
-      unsigned fail = __ballot_sync(kFull, lane < cnt && !(sl.flags[start + lane] & kFlagConverged));
-      const int W64 = (cd.dc.n + 63) / 64;
-      while (fail) {
-        const int l = __ffs(fail) - 1;
-        fail &= fail - 1;
-        const int f = start + l;
-        osd_one_frame(S, cd.dc.n, cd.dc.k, cd.M, cd.std_cols, sl.llr + size_t(f) * sl.ld, a.order,
-                      sl.hard + size_t(f) * W64, sl.flags + f);
-      }
+    for (unsigned fm = fail; fm; fm &= fm - 1) {
+      const int l = __ffs(fm) - 1;
+      const int sl_l = __shfl_sync(kFull, slot, l);
+      const int f_l = __shfl_sync(kFull, f, l);
+      const SrvSlot sl = load_slot(a.slots + sl_l);
+      const int W64 = (n + 63) / 64;
+      osd_one_frame(S, n, cd.dc.k, cd.M, cd.std_cols, sl.llr + size_t(f_l) * sl.ld, a.order,
+                    sl.hard + size_t(f_l) * W64, sl.flags + f_l);
     }
-    __syncwarp();
-    if (lane == 0) {
+    // ---- count finished frames; the frame that completes a request posts it
+    if (done) {
       __threadfence();
-      const unsigned d = atomicAdd(&a.slots[slot].done, unsigned(cnt)) + unsigned(cnt);
+      const SrvSlot sl = load_slot(a.slots + slot);
+      const unsigned d = atomicAdd(&a.slots[slot].done, 1u) + 1u;
       if (int(d) == sl.F) {
         const unsigned ci = atomicAdd(&a.dv->comp_tail, 1u);
         SrvComp *c = a.comp + (ci % unsigned(a.ring));
@@ -269,8 +323,9 @@ __global__ void __launch_bounds__(32) serve_kernel(const SrvArgs a) {
         __threadfence_system();
         *reinterpret_cast<volatile unsigned *>(&c->seq) = ci + 1;
       }
+      f = -1;
+      slot = -1;
     }
-    idle_since = globaltimer();
   }
   if (lane == 0) {
     if (atomicSub(&a.dv->live, 1u) == 1u) {
@@ -316,9 +371,10 @@ struct bch_server {
   std::vector<unsigned> slot_gen;
   SrvSlot *slot_mirror = nullptr;         // pinned host copies of the slot descriptors
   std::vector<cudaEvent_t> slot_ev;       // per slot: its admission copies are done
-  std::deque<unsigned> staged;            // ring entries whose copies are in flight, in order
+  std::deque<std::pair<unsigned, int>> staged;  // (ring entry, code) with copies in flight
   long long published_open = 0;           // published requests not yet completed
-  unsigned sub_tail = 0, comp_read = 0;
+  unsigned sub_tail[kSrvMaxCodes] = {};
+  unsigned comp_read = 0;
   unsigned long long next_id = 1;
   int blocks = 0;
   size_t smem = 0;
@@ -410,14 +466,16 @@ bch_status ensure_running(bch_server *s) {
 bch_status publish_staged(bch_server *s) {
   bool any = false;
   while (!s->staged.empty()) {
-    const unsigned entry = s->staged.front();
+    const unsigned entry = s->staged.front().first;
+    const int code = s->staged.front().second;
     const cudaError_t e = cudaEventQuery(s->slot_ev[entry & 0xffffu]);
     if (e == cudaErrorNotReady) break;
     if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("admission copies: ") + cudaGetErrorString(e));
-    s->sub_ring[s->sub_tail % unsigned(s->cfg.max_requests)] = entry;
+    const unsigned R = unsigned(s->cfg.max_requests);
+    s->sub_ring[size_t(code) * R + s->sub_tail[code] % R] = entry;
     std::atomic_thread_fence(std::memory_order_release);
-    s->sub_tail++;
-    s->sh->sub_tail = s->sub_tail;
+    s->sub_tail[code]++;
+    s->sh->sub_tail[code] = s->sub_tail[code];
     s->staged.pop_front();
     s->published_open++;
     any = true;
@@ -462,7 +520,7 @@ bch_status admit(bch_server *s, bch_server::Req &r, bool *admitted) {
     e = cudaMemcpyAsync(s->slots_dev + r.slot, &sl, sizeof(sl), cudaMemcpyHostToDevice, s->cst);
   if (e == cudaSuccess) e = cudaEventRecord(s->slot_ev[r.slot], s->cst);
   if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("admission copies: ") + cudaGetErrorString(e));
-  s->staged.push_back(unsigned(r.slot) | (gen << 16));
+  s->staged.emplace_back(unsigned(r.slot) | (gen << 16), r.code);
   s->stats.admitted++;
   s->stats.bytes_in_use += L.total;
   *admitted = true;
@@ -524,7 +582,7 @@ bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
   const int R = cfg->max_requests;
   // host-mapped control block, submission ring and completion ring in one allocation
   const size_t ring_off = 64;
-  const size_t comp_off = (ring_off + size_t(R) * 4 + 63) & ~size_t(63);
+  const size_t comp_off = (ring_off + size_t(kSrvMaxCodes) * R * 4 + 63) & ~size_t(63);
   const size_t shared_bytes = comp_off + size_t(R) * sizeof(SrvComp);
   void *hp = nullptr;
   if (cudaHostAlloc(&hp, shared_bytes, cudaHostAllocMapped) != cudaSuccess) {
@@ -637,7 +695,9 @@ bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
     cleanup();
     return fail(BCH_ECUDA, "streams");
   }
-  s->smem = std::max(sizeof(float) * 128 * 32 * 2 + sizeof(uint32_t) * 9 * 32, sizeof(OsdSmem));
+  // per warp: y and accumulator columns (128 x 32 FP32 each), OSD scratch,
+  // automorphism parameters [9][32], claim segments [3][32]
+  s->smem = sizeof(float) * 128 * 32 * 2 + sizeof(OsdSmem) + sizeof(uint32_t) * 9 * 32 + sizeof(int) * 3 * 32;
   if (cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s->smem)) !=
       cudaSuccess) {
     cleanup();
