@@ -1,5 +1,9 @@
 // Host-memory decode pipeline (bch_decoder): chunked copy-in / hybrid decode /
 // copy-out on two CUDA streams so transfers overlap the kernels of the other chunk.
+// Chunks alternate between two device buffer sets; stream order makes a buffer's next
+// copy-in wait for its previous copy-out.  With pinned host memory a GB300 moves
+// about 210 GB/s each way, so chunks of ~256k frames keep the copies hidden behind
+// the decode.
 #include <cstring>
 #include <new>
 #include <string>
