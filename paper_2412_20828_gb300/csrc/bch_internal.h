@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -78,6 +79,15 @@ struct bch_code {
   void *dev_blob = nullptr;  // device allocation holding the arrays below
   bchlib::DevCode dc;        // host-side descriptor with device pointers
   bchlib::DevCode *dev_dc = nullptr;  // descriptor copy in device memory
+  // specialised kernels already looked up for this code, by (format, tuning knobs):
+  // spares regenerating the kernel source on every decode call
+  struct JitMemo {
+    std::string key;
+    void *kernel;
+    std::string err;
+  };
+  mutable std::vector<JitMemo> jit_memo;
+  mutable std::mutex jit_mu;
 };
 
 namespace bchlib {

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -424,13 +425,38 @@ static cudaError_t launch_jit(cudaKernel_t k, const bch_code *code, const NmsArg
                       size_t(tpb) * (size_t(a.P) * 4 + size_t(n) * (sa + sy) + size_t(scr) * sa);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   const void *fn = reinterpret_cast<const void *>(k);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
+  // launch configuration, looked up once per (device, kernel, shared memory size)
+  struct LaunchCfg {
+    int dev;
+    const void *fn;
+    size_t smem;
+    int sms, per_sm;
+  };
+  static std::mutex cfg_mu;
+  static std::vector<LaunchCfg> cfgs;
   int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tpb, smem);
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  bool found = false;
+  {
+    std::lock_guard<std::mutex> lk(cfg_mu);
+    for (const LaunchCfg &c : cfgs)
+      if (c.dev == dev && c.fn == fn && c.smem == smem) {
+        sms = c.sms;
+        per_sm = c.per_sm;
+        found = true;
+        break;
+      }
+  }
+  if (!found) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tpb, smem);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(cfg_mu);
+    cfgs.push_back({dev, fn, smem, sms, per_sm});
+  }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long blocks = (long long)sms * per_sm;
   const long long need = (a.F + tpb - 1) / tpb;

@@ -351,7 +351,37 @@ static void write_file_atomic(const std::string &path, const std::vector<char> &
 
 // Returns the specialised kernel for (code, msg), compiling it on first use (or
 // loading it from the on-disk cache); on failure returns nullptr and sets *err.
+cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err);
+
+// The tuning knobs that shape the generated source (read from the environment).
+static std::string jit_knob_signature(int n) {
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d", jit_block_size(n), jit_min_blocks(n), int(jit_pairs()),
+                jit_fma_percent(), env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, 0), jit_scratch_words(n));
+  return buf;
+}
+
 cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
+  const std::string key = std::to_string(msg) + ":" + jit_knob_signature(c->alg.n);
+  {
+    std::lock_guard<std::mutex> lk(c->jit_mu);
+    for (const auto &m : c->jit_memo)
+      if (m.key == key) {
+        if (!m.kernel) *err = m.err;
+        return static_cast<cudaKernel_t>(m.kernel);
+      }
+  }
+  std::string why;
+  cudaKernel_t k = jit_kernel_from_source(c, msg, &why);
+  {
+    std::lock_guard<std::mutex> lk(c->jit_mu);
+    c->jit_memo.push_back({key, static_cast<void *>(k), why});
+  }
+  if (!k) *err = why;
+  return k;
+}
+
+cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err) {
   const std::string src = jit_source(c, msg);
   std::shared_ptr<Compiled> cp;
   {

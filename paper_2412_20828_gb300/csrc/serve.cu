@@ -842,7 +842,8 @@ void bch_server_destroy(bch_server *s) {
 // same arrival stream through plain batched launches instead of the server: requests
 // are collected until batch_us after the first one or batch_frames frames, then every
 // code's share is copied in, hybrid-decoded with one bch_hybrid_decode call and copied
-// back before the batch's requests complete.
+// back before the batch's requests complete.  Without standard matrices or with
+// osd_order = 0 the batches run the NMS decoder alone (n_autos = 0: the plain decoder).
 bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch_serve_bench_result *res) {
   if (!c || !res || !c->pools || !c->pool_frames || !c->lds || !c->codes || c->n_codes < 1 ||
       c->n_codes > kSrvMaxCodes || c->rate_rps <= 0 || c->duration_s <= 0 || c->max_frames < 1)
@@ -988,14 +989,21 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
           if (r.code != k) continue;
           cudaMemcpyAsync(dllr[k] + size_t(tot) * c->lds[k], c->pools[k] + size_t(r.off) * c->lds[k],
                           size_t(r.F) * c->lds[k] * 4, cudaMemcpyDefault, st);
-          bch_draw_automorphisms(c->codes[k]->alg.n, p.n_autos, c->seed ^ 0x5A5Aull, uint64_t(r.off), r.F,
-                                 daut[k] + size_t(tot) * p.n_autos, st);
+          if (p.n_autos > 0)
+            bch_draw_automorphisms(c->codes[k]->alg.n, p.n_autos, c->seed ^ 0x5A5Aull, uint64_t(r.off), r.F,
+                                   daut[k] + size_t(tot) * p.n_autos, st);
           tot += r.F;
         }
         if (!tot) continue;
-        bch_status s2 = bch_hybrid_decode(c->codes[k], c->std_codes ? c->std_codes[k] : nullptr, &p, dllr[k],
-                                          c->lds[k], tot, daut[k], dhard[k], dit[k], dfl[k], nullptr, nullptr,
-                                          nullptr, dws[k], st);
+        // the hybrid decoder, or (no OSD) the NMS decoder alone -- with n_autos = 0 the
+        // single plain decoder on the given matrices
+        bch_status s2 = (c->std_codes && p.osd_order > 0)
+                            ? bch_hybrid_decode(c->codes[k], c->std_codes[k], &p, dllr[k], c->lds[k], tot,
+                                                daut[k], dhard[k], dit[k], dfl[k], nullptr, nullptr, nullptr,
+                                                dws[k], st)
+                            : bch_nms_decode(c->codes[k], &p, dllr[k], c->lds[k], tot,
+                                             p.n_autos > 0 ? daut[k] : nullptr, dhard[k], dit[k], dfl[k],
+                                             nullptr, dws[k], st);
         if (s2 != BCH_OK) return s2;
         const int W64 = (c->codes[k]->alg.n + 63) / 64;
         cudaMemcpyAsync(hbuf + size_t(k) * capF * 2, dhard[k], size_t(tot) * W64 * 8, cudaMemcpyDeviceToHost, st);
