@@ -47,6 +47,41 @@ bch_status fail(bch_status s, const std::string &msg) {
 
 }  // namespace bchlib
 
+namespace bchlib {
+cudaError_t launch_geometry(const void *fn, int tpb, size_t smem, int *sms, int *per_sm) {
+  struct Geo {
+    int dev;
+    const void *fn;
+    int tpb;
+    size_t smem;
+    int sms, per_sm;
+  };
+  static std::mutex mu;
+  static std::vector<Geo> known;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Geo &g : known)
+      if (g.dev == dev && g.fn == fn && g.tpb == tpb && g.smem == smem) {
+        *sms = g.sms;
+        *per_sm = g.per_sm;
+        return cudaSuccess;
+      }
+  }
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, tpb, smem);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  known.push_back({dev, fn, tpb, smem, *sms, *per_sm});
+  return cudaSuccess;
+}
+}  // namespace bchlib
+
 namespace {
 
 bch_status cuda_fail(cudaError_t e, const char *what) {
@@ -417,6 +452,7 @@ bch_status bch_workspace_size(const bch_code *code, const bch_nms_params *params
   return BCH_OK;
 }
 
+
 static cudaError_t launch_jit(cudaKernel_t k, const bch_code *code, const NmsArgs &a, cudaStream_t st) {
   const int n = code->alg.n, tpb = jit_block_size(n), scr = jit_scratch_words(n);
   const size_t sa = a.msg == BCH_MSG_INT8 ? 4 : 4;
@@ -425,38 +461,9 @@ static cudaError_t launch_jit(cudaKernel_t k, const bch_code *code, const NmsArg
                       size_t(tpb) * (size_t(a.P) * 4 + size_t(n) * (sa + sy) + size_t(scr) * sa);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   const void *fn = reinterpret_cast<const void *>(k);
-  // launch configuration, looked up once per (device, kernel, shared memory size)
-  struct LaunchCfg {
-    int dev;
-    const void *fn;
-    size_t smem;
-    int sms, per_sm;
-  };
-  static std::mutex cfg_mu;
-  static std::vector<LaunchCfg> cfgs;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  int sms = 0, per_sm = 0;
+  cudaError_t e = launch_geometry(fn, tpb, smem, &sms, &per_sm);
   if (e != cudaSuccess) return e;
-  bool found = false;
-  {
-    std::lock_guard<std::mutex> lk(cfg_mu);
-    for (const LaunchCfg &c : cfgs)
-      if (c.dev == dev && c.fn == fn && c.smem == smem) {
-        sms = c.sms;
-        per_sm = c.per_sm;
-        found = true;
-        break;
-      }
-  }
-  if (!found) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tpb, smem);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lk(cfg_mu);
-    cfgs.push_back({dev, fn, smem, sms, per_sm});
-  }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long blocks = (long long)sms * per_sm;
   const long long need = (a.F + tpb - 1) / tpb;

@@ -98,13 +98,9 @@ cudaError_t launch_compact(const uint8_t *flags, int F, uint32_t *counts, uint32
 }
 
 cudaError_t launch_osd(const OsdArgs &a, cudaStream_t st) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int sms = 0, per_sm = 0;
   const size_t smem = sizeof(OsdSmem) * kOsdWarps;
-  cudaError_t e = cudaFuncSetAttribute(osd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, osd_kernel, 32 * kOsdWarps, smem);
+  cudaError_t e = launch_geometry(reinterpret_cast<const void *>(osd_kernel), 32 * kOsdWarps, smem, &sms, &per_sm);
   if (e != cudaSuccess) return e;
   long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
   const long long need = (a.max_frames + kOsdWarps - 1) / kOsdWarps;
