@@ -123,7 +123,11 @@ def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, 
                             "fer": (c[vi, si, :, 1] / fr).tolist(),
                             "ber": (c[vi, si, :, 2] / (fr * n)).tolist(),
                             "avg_iters": (c[vi, si, :, 5] / fr).tolist(),
-                            "frames_per_s": (fr / np.maximum(dev_s[vi, si], 1e-12)).tolist()}
+                            "frames_per_s": (fr / np.maximum(dev_s[vi, si], 1e-12)).tolist(),
+                            # edge-updates per second: NMS iterations run x P x edges over
+                            # the stage's device time (OSD time included for the hybrid)
+                            "edge_updates_per_s": (c[vi, si, :, 5] * n_autos * code.edges /
+                                                   np.maximum(dev_s[vi, si], 1e-12)).tolist()}
             entry["variants"][name] = v
         for stage in ("nms", "hybrid") if hybrid else ("nms",):
             ref = entry["variants"]["fp32"][stage]["fer"]
