@@ -220,16 +220,36 @@ __device__ __forceinline__ void osd_one_frame_t(OsdSmem &S, int n, int K, int M,
     // reaches either best can at most tie it with a larger index: it cannot be chosen.
     unsigned long long bound1 = best.s;
     for (int off = 16; off > 0; off >>= 1) bound1 = min(bound1, __shfl_xor_sync(kFull, bound1, off));
-    for (int x = 0; x + 1 < K; x++) {
-      const unsigned long long wa = S.wm[x];
-      if (wa + S.wm[x + 1] >= bound1) break;  // no pair (x' >= x, y > x') can win
-      const unsigned long long Da = D0 ^ S.colbits[x];
-      const uint32_t base = uint32_t(1 + K) + uint32_t(x * K - x * (x + 1) / 2);
-      for (int y = x + 1 + lane; y < K; y += 32) {
-        const unsigned long long lb = wa + S.wm[y];
-        if (lb >= bound1 || lb >= best.s) break;  // later y only raise the bound
-        const unsigned long long s = lb + wsum(S, Da ^ S.colbits[y], nch);
-        consider(best, s, base + uint32_t(y - x - 1), uint32_t(x + 1) | (uint32_t(y + 1) << 8));
+    // The pairs (x < y) in enumeration order form one flat sequence; lane l takes pairs
+    // l, l + 32, l + 64, ... so every lane stays busy across the short rows of the
+    // triangle.  p is the pair's position, (x, y) the pair.
+    uint32_t p = uint32_t(lane);
+    int x = 0, y = 1 + lane;
+    while (x + 1 < K && y >= K) {  // row x holds y = x + 1 .. K - 1
+      y = y - K + x + 2;
+      x++;
+    }
+    unsigned long long wa = 0, ca = 0;
+    int xa = -1;
+    while (x + 1 < K) {
+      if (x != xa) {
+        wa = S.wm[x];
+        ca = D0 ^ S.colbits[x];
+        xa = x;
+      }
+      const unsigned long long cap = min(bound1, best.s);
+      // every later pair of this lane has x' >= x, so its bound is >= wm[x] + wm[x + 1]
+      if (wa + S.wm[x + 1] >= cap) break;
+      const unsigned long long lb = wa + S.wm[y];
+      if (lb < cap) {
+        const unsigned long long s = lb + wsum(S, ca ^ S.colbits[y], nch);
+        consider(best, s, uint32_t(1 + K) + p, uint32_t(x + 1) | (uint32_t(y + 1) << 8));
+      }
+      p += 32;
+      y += 32;
+      while (x + 1 < K && y >= K) {
+        y = y - K + x + 2;
+        x++;
       }
     }
   }
