@@ -131,6 +131,14 @@ def oracle_sample(frames_per_point, threads):
     return res, total_frames, dt
 
 
+_T0 = time.time()
+
+
+def progress(msg):
+    """A timestamped progress line on stderr (stdout carries only the JSON line)."""
+    print(f"# bench {time.time() - _T0:7.1f} s: {msg}", file=sys.stderr, flush=True)
+
+
 def clopper_pearson(k, n, a=0.05):
     from scipy.stats import beta
     lo = 0.0 if k == 0 else beta.ppf(a / 2, k, n - k + 1)
@@ -190,9 +198,12 @@ def run_serving(B, torch, dev, seconds, rate):
                    budget_bytes=16 << 30, max_requests=8192, max_frames_per_request=4096)
     # warm-up: a short stream
     B.serve_bench(srv, codes, stds, pools, rate, 0.5, seed=11)
+    progress("serving: server at the configured rate")
     res = B.serve_bench(srv, codes, stds, pools, rate, seconds, seed=12)
+    progress("serving: static batching at the configured rate")
     stat = B.serve_bench(None, codes, stds, pools, rate, seconds, seed=12, static_batching=True,
                          batch_us=1000, batch_frames=65536)
+    progress("serving: below saturation")
     # the same stream below saturation: half the request rate the slower of the two served
     sub = 0.5 * min(res["requests"] / res["elapsed_s"], stat["requests"] / stat["elapsed_s"], rate)
     res_sub = B.serve_bench(srv, codes, stds, pools, sub, seconds, seed=13)
@@ -204,6 +215,7 @@ def run_serving(B, torch, dev, seconds, rate):
     # in static batches, at both rates
     plain = {}
     for key, r_ in (("config_rate", rate), ("below_saturation", sub)):
+        progress(f"serving: static plain decoder, {key}")
         plain[key] = B.serve_bench(None, stds, None, pools, r_, seconds, seed=12 if key == "config_rate" else 13,
                                    iters=8, n_autos=0, osd_order=0, static_batching=True,
                                    batch_us=1000, batch_frames=65536)
@@ -318,6 +330,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
+    progress("building codes and generating frames")
     # ---- per-code state, frames generated on the device before timing
     states = []
     for (n, k) in CODES:
@@ -436,6 +449,7 @@ def main():
                 "edge_updates_per_s": eups, "nms_ms_per_step": nms_time * 1e3,
                 "peak_basis": f"{sms} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock under load)"}
 
+    progress("device-timed steps done")
     # ---- end to end through the host pipeline (bch_decoder), copies inside the timing
     e2e = None
     if not args.no_e2e:
@@ -467,6 +481,7 @@ def main():
         for d in dec:
             d.close()
 
+    progress("end-to-end done")
     # ---- serving: mixed-code Poisson stream, server vs static batching
     serving = None
     if rank == 0 and args.serve_seconds > 0:
@@ -475,14 +490,17 @@ def main():
         except B.BchError as e:  # reported in the line; the decode throughput stands
             serving = {"error": str(e)}
 
+    progress("serving done")
     # ---- plain NMS on the standard matrix (the single-decoder configuration)
     plain = run_plain(B, torch, dev) if rank == 0 and not args.no_plain else None
 
+    progress("single decoder done")
     # ---- training: per-iteration alpha_t of BCH(127,64) through the backward kernel
     training = None
     if rank == 0 and args.train_steps > 0:
         training = run_training(B, torch, args.train_steps)
 
+    progress("training done")
     # ---- CPU baseline: the oracle on a bounded sample, and FER agreement
     cpu = None
     fer_match = None
@@ -490,6 +508,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         threads = os.cpu_count() or 1
         res, nf, dt = oracle_sample(args.cpu_frames_per_point, threads)
+        progress("CPU baseline: all cores done, one core next")
         _, nf1, dt1 = oracle_sample(max(4, args.cpu_frames_per_point // 20), 1)
         cpu = {"value": nf / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_frames_per_point} frames per point x 11 points x 2 codes "

@@ -45,8 +45,9 @@ struct BwdArgs {
 };
 
 // Resident blocks per SM and SM count for (fn, block size, dynamic shared memory) on the
-// current device; sets the kernel's shared-memory limit.  Looked up once per
-// (device, fn, smem) and remembered, so repeated launches cost no driver queries.
+// current device; raises the kernel's shared-memory limit when this launch needs more
+// than any before.  Remembered per combination, so repeated launches cost no driver
+// queries.
 cudaError_t launch_geometry(const void *fn, int tpb, size_t smem, int *sms, int *per_sm);
 cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st);
 cudaError_t launch_osd(const OsdArgs &a, cudaStream_t st);

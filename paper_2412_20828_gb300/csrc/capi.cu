@@ -49,6 +49,15 @@ bch_status fail(bch_status s, const std::string &msg) {
 
 namespace bchlib {
 cudaError_t launch_geometry(const void *fn, int tpb, size_t smem, int *sms, int *per_sm) {
+  // The shared-memory limit is one attribute per function (per device): it holds the
+  // last value set, so it is raised to the largest size any launch has needed and never
+  // lowered.  Occupancy depends on (block size, shared memory) and is remembered per
+  // combination.
+  struct Limit {
+    int dev;
+    const void *fn;
+    size_t smem_max;
+  };
   struct Geo {
     int dev;
     const void *fn;
@@ -57,26 +66,34 @@ cudaError_t launch_geometry(const void *fn, int tpb, size_t smem, int *sms, int 
     int sms, per_sm;
   };
   static std::mutex mu;
+  static std::vector<Limit> limits;
   static std::vector<Geo> known;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    for (const Geo &g : known)
-      if (g.dev == dev && g.fn == fn && g.tpb == tpb && g.smem == smem) {
-        *sms = g.sms;
-        *per_sm = g.per_sm;
-        return cudaSuccess;
-      }
+  std::lock_guard<std::mutex> lk(mu);
+  Limit *lim = nullptr;
+  for (Limit &l : limits)
+    if (l.dev == dev && l.fn == fn) lim = &l;
+  if (!lim || lim->smem_max < smem) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    if (lim) {
+      lim->smem_max = smem;
+    } else {
+      limits.push_back({dev, fn, smem});
+    }
   }
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
+  for (const Geo &g : known)
+    if (g.dev == dev && g.fn == fn && g.tpb == tpb && g.smem == smem) {
+      *sms = g.sms;
+      *per_sm = g.per_sm;
+      return cudaSuccess;
+    }
   e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, tpb, smem);
   if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lk(mu);
   known.push_back({dev, fn, tpb, smem, *sms, *per_sm});
   return cudaSuccess;
 }

@@ -963,7 +963,12 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
         return fail(BCH_ENOMEM, "static batching buffers");
     }
     size_t next = 0;
+    bch_status sfail = BCH_OK;
     while (next < reqs.size()) {
+      if (now_s() > c->duration_s * 10 + 30) {
+        sfail = fail(BCH_ETIMEOUT, "static batching benchmark did not drain");
+        break;
+      }
       // wait for the first request of the batch, then collect
       double tn = now_s();
       if (reqs[next].t_arr > tn) {
@@ -1004,13 +1009,20 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
                             : bch_nms_decode(c->codes[k], &p, dllr[k], c->lds[k], tot,
                                              p.n_autos > 0 ? daut[k] : nullptr, dhard[k], dit[k], dfl[k],
                                              nullptr, dws[k], st);
-        if (s2 != BCH_OK) return s2;
+        if (s2 != BCH_OK) {
+          sfail = s2;
+          break;
+        }
         const int W64 = (c->codes[k]->alg.n + 63) / 64;
         cudaMemcpyAsync(hbuf + size_t(k) * capF * 2, dhard[k], size_t(tot) * W64 * 8, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(ibuf + size_t(k) * capF, dit[k], tot, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(fbuf + size_t(k) * capF, dfl[k], tot, cudaMemcpyDeviceToHost, st);
       }
-      if (cudaStreamSynchronize(st) != cudaSuccess) return fail(BCH_ECUDA, "static batch");
+      if (sfail != BCH_OK) break;
+      if (cudaStreamSynchronize(st) != cudaSuccess) {
+        sfail = fail(BCH_ECUDA, "static batch");
+        break;
+      }
       tn = now_s();
       for (size_t q = next; q < end; q++) {
         lat.push_back(tn - reqs[q].t_arr);
@@ -1018,6 +1030,7 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
       }
       next = end;
     }
+    cudaStreamSynchronize(st);
     for (int k = 0; k < nc; k++) {
       cudaFree(dllr[k]);
       cudaFree(daut[k]);
@@ -1027,6 +1040,7 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
       cudaFree(dws[k]);
     }
     cudaStreamDestroy(st);
+    if (sfail != BCH_OK) return sfail;
   }
   const double el = now_s();
   std::sort(lat.begin(), lat.end());
