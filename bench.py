@@ -456,7 +456,7 @@ def main():
         dec = []
         host = []
         for st in states:
-            dec.append(B.HostDecoder(st["code"], st["std"], st["p"], ld, chunk_frames=1 << 18))
+            dec.append(B.HostDecoder(st["code"], st["std"], st["p"], ld, chunk_frames=1 << 20))
             hl = torch.empty((F, ld), dtype=torch.float32, pin_memory=True)
             hl.copy_(st["llr"].cpu())
             hh = torch.empty((F, 1), dtype=torch.int64, pin_memory=True)
@@ -470,7 +470,8 @@ def main():
                 t0 = time.perf_counter()
             # one call per code over all its frames: the pipeline overlaps each chunk's
             # copy-in with the previous chunk's decode (automorphisms drawn from the
-            # frames' position in the call)
+            # frames' position in the call); 1M-frame chunks keep the number of decode
+            # launches, each ending in a tail of slow frames, small
             for d, (hl, hh, hi, hf), st in zip(dec, host, states):
                 d.run(hl, SEED_AUTOS, st["base"], hh, hi, hf)
         t1 = time.perf_counter()

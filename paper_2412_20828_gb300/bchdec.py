@@ -394,7 +394,7 @@ def train_alpha(code: Code, n_autos, iters, alpha, steps, batch, ebn0_lo, ebn0_h
 class HostDecoder:
     """bch_decoder: decodes frames held in host memory with overlapped transfers."""
 
-    def __init__(self, code: Code, std_code, p: NmsParams, ld: int, chunk_frames: int = 1 << 18):
+    def __init__(self, code: Code, std_code, p: NmsParams, ld: int, chunk_frames: int = 1 << 20):
         self._h = C.c_void_p()
         self._p = p
         self.code, self.std = code, std_code

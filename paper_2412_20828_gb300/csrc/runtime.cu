@@ -2,8 +2,9 @@
 // copy-out on two CUDA streams so transfers overlap the kernels of the other chunk.
 // Chunks alternate between two device buffer sets; stream order makes a buffer's next
 // copy-in wait for its previous copy-out.  With pinned host memory a GB300 moves
-// about 210 GB/s each way, so chunks of ~256k frames keep the copies hidden behind
-// the decode.
+// about 210 GB/s each way; chunks of ~1M frames keep the copies hidden behind the
+// decode while keeping few decode launches (each ends in a tail where the slowest
+// frames of the last wave finish on a partly idle GPU).
 #include <cstring>
 #include <new>
 #include <string>
