@@ -464,6 +464,7 @@ def main():
             hf = torch.empty(F, dtype=torch.uint8, pin_memory=True)
             host.append((hl, hh, hi, hf))
         e2e_steps = max(2, min(args.steps, 5))
+        code_s = [0.0] * len(states)
         for s in range(1 + e2e_steps):
             if s == 1:
                 torch.cuda.synchronize()
@@ -472,13 +473,17 @@ def main():
             # copy-in with the previous chunk's decode (automorphisms drawn from the
             # frames' position in the call); 1M-frame chunks keep the number of decode
             # launches, each ending in a tail of slow frames, small
-            for d, (hl, hh, hi, hf), st in zip(dec, host, states):
+            for ci, (d, (hl, hh, hi, hf), st) in enumerate(zip(dec, host, states)):
+                tc = time.perf_counter()
                 d.run(hl, SEED_AUTOS, st["base"], hh, hi, hf)
+                if s >= 1:
+                    code_s[ci] += time.perf_counter() - tc
         t1 = time.perf_counter()
         e2e_v = frames_per_step * world / ((t1 - t0) / e2e_steps)
         e2e = {"value": e2e_v, "unit": "frames/s",
                "h2d_bytes_per_step": int(frames_per_step * ld * 4),
-               "d2h_bytes_per_step": int(frames_per_step * (8 + 2))}
+               "d2h_bytes_per_step": int(frames_per_step * (8 + 2)),
+               "ms_per_code_call": [round(x / e2e_steps * 1e3, 2) for x in code_s]}
         for d in dec:
             d.close()
 
