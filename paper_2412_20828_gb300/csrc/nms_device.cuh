@@ -388,6 +388,7 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
 #pragma unroll
     for (int w = 0; w < NW; w++) cb[w] = 0;
     if constexpr (MSG == kFP32) {
+      float mx = 0.0f;
 #pragma unroll
       for (int i = 0; i < NW * 32; i++) {
         if (i < n) {
@@ -395,7 +396,17 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
           y[i * kShift] = yn;
           acc[i * kShift] = 0.0f;
           cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
+          mx = fmaxf(mx, fabsf(yn));
         }
+      }
+      // y grows about tenfold per iteration; past 2^100 the frame is scaled by 2^-64
+      // (exact, and min-sum is scale invariant) so that long decodes of high-degree
+      // codes cannot overflow FP32.  Not in training, whose checkpoints are in LLR units.
+      if (mx > 0x1p100f && !a.ckpt && f >= 0) {
+#pragma unroll
+        for (int i = 0; i < NW * 32; i++)
+          if (i < n) y[i * kShift] *= 0x1p-64f;
+        escale += 64;
       }
     } else {
       // pass 1: FP32 merge into the accumulator slot, track the magnitude
@@ -449,10 +460,8 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
       if (a.flags) a.flags[f] = nz ? 0 : uint8_t(kFlagConverged);
       if (a.llr_out) {
         float *dst = a.llr_out + size_t(f) * a.ld;
-        float unscale = 1.0f;
-        if constexpr (MSG == kINT8) unscale = 0.25f;
-        for (int k = 0; k < escale; k++) unscale *= 2.0f;
-        for (int i = 0; i < n; i++) dst[i] = float(ld_y(y + (i * kShift))) * unscale;
+        const float unit = MSG == kINT8 ? 0.25f : 1.0f;
+        for (int i = 0; i < n; i++) dst[i] = ldexpf(float(ld_y(y + (i * kShift))) * unit, escale);
       }
       need = true;
     }

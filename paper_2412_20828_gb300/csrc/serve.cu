@@ -279,12 +279,16 @@ __global__ void __launch_bounds__(32) serve_kernel(const SrvArgs a) {
         case 32: srv_copies<32>(cd, a.P, y + lane, acc + lane, ctx + lane, alpha); break;
         default: srv_copies<48>(cd, a.P, y + lane, acc + lane, ctx + lane, alpha); break;
       }
+      float mx = 0.0f;
       for (int i = 0; i < n; i++) {
         const float yn = __fmaf_rn(acc[i * 32 + lane], invP, y[i * 32 + lane]);
         y[i * 32 + lane] = yn;
         acc[i * 32 + lane] = 0.0f;
         cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
+        mx = fmaxf(mx, fabsf(yn));
       }
+      if (mx > 0x1p100f)  // exact renormalisation against FP32 overflow (see the batch kernels)
+        for (int i = 0; i < n; i++) y[i * 32 + lane] *= 0x1p-64f;
       t++;
       nz = syndrome_nonzero<4>(reinterpret_cast<const uint4 *>(cd.dc.rowmask), cd.dc.rows, cb);
       done = t >= a.iters || (a.early_stop && nz == 0);

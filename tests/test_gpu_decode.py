@@ -394,3 +394,32 @@ def test_bch15_hybrid_and_osd_vs_exhaustive_ml(torch_cuda, ebn0):
     excess = err_h & ~err_ml  # the hybrid errs where ML does not
     assert int((excess & ~undetected).sum()) <= 0.01 * e_ml + 3, (e_h, e_ml)
     assert abs(e_o - e_ml) <= 0.01 * e_ml + 3 * np.sqrt(e_o + e_ml), (e_o, e_ml)
+
+
+@pytest.mark.parametrize("nk", [(63, 36), (127, 64)])
+def test_maximum_iterations_no_overflow(torch_cuda, nk):
+    """The API's largest iteration count without early stop: y grows about tenfold per
+    iteration (past the FP32 range for BCH(127,64) after 32 iterations), and the decoder
+    renormalises exactly by powers of two, so decisions and final LLRs still follow the
+    FP64 oracle."""
+    n, k = nk
+    c = code(n, k)
+    F = 200
+    cw, llr = frames(n, k, F, 2.0, 5, ld=(n + 3) & ~3)
+    autos = O.draw_autos(n, 3, 1, 0, F)
+    g = run_nms(torch_cuda, c, llr, autos, 32, 0.78, early_stop=False)
+    ref = O.nms_enhanced(c.dense(), llr, autos, 32, 0.78, early_stop=False, trace=True, threads=None)
+    ok = ~ambiguous_frames(llr, ref, n)
+    assert ok.mean() > 0.8
+    y = g["y"][:, :n].astype(np.float64)
+    assert not np.any(np.isnan(y))
+    assert np.array_equal(g["hard"][ok], ref["hard"][ok])
+    assert np.all(g["iters"] == 32)
+    # the FP32 output holds +-inf only where the final LLR is at the FP32 range's edge
+    inf = np.isinf(y)
+    assert np.all(np.abs(ref["y"][inf]) > 1e38)
+    assert np.all(np.sign(y[inf]) == np.sign(ref["y"][inf]))
+    env = frame_envelope(ref)[:, None]
+    err = np.abs(y - ref["y"]) / (TRAJ_TOL * np.maximum(np.abs(ref["y"]), env))
+    sel = ok[:, None] & ~inf
+    assert err[sel].max() <= 1.0
