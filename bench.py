@@ -193,7 +193,20 @@ def run_serving(B, torch, dev, seconds, rate):
         h = torch.empty((pool_frames, ld), dtype=torch.float32, pin_memory=True)
         h.copy_(d.cpu())
         pools.append(h)
+    # compile and load every code's specialised kernel before any timed stream (on a
+    # fresh machine the n = 127 kernels take tens of seconds to compile)
+    for c, std, h in zip(codes, stds, pools):
+        nw = 4096
+        dl = h[:nw].to(dev)
+        aut = torch.empty((nw, P_AUTOS), dtype=torch.int16, device=dev)
+        B.draw_automorphisms(c.n, P_AUTOS, 1, 0, aut)
+        hd = torch.empty((nw, (c.n + 63) // 64), dtype=torch.int64, device=dev)
+        it = torch.empty(nw, dtype=torch.uint8, device=dev)
+        fl = torch.empty(nw, dtype=torch.uint8, device=dev)
+        B.hybrid_decode(c, std, B.params(ITERS, ALPHA, n_autos=P_AUTOS, osd_order=OSD_ORDER), dl, aut, hd,
+                        it, fl)
     torch.cuda.synchronize()
+    progress("serving: kernels ready")
     srv = B.Server(codes, stds, ITERS, ALPHA, n_autos=P_AUTOS, osd_order=OSD_ORDER,
                    budget_bytes=16 << 30, max_requests=8192, max_frames_per_request=4096)
     # warm-up: a short stream
