@@ -38,10 +38,10 @@ METRIC = "frames/s & edge-updates/s on 1 GB300 at oracle-matched FER; served p50
 LANE_OPS_PER_EDGE = 8  # min1/min2 (3), sign (1), output select (2), accumulate (1), gather (1)
 # DRAM bytes per decoded frame of the specialised NMS kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a 1.1 M-frame BCH(63,36) launch:
-# 288.35 MB + 10.28 MB.  Traffic grows with the frames a launch decodes (each frame's
+# 288.36 MB + 10.23 MB.  Traffic grows with the frames a launch decodes (each frame's
 # LLRs are read once, its results written once), so a launch's traffic is this figure
 # times its frames.  Set to None when the kernel changes until it is re-captured.
-JIT_DRAM_BYTES_PER_FRAME = (288.35e6 + 10.28e6) / 1.1e6
+JIT_DRAM_BYTES_PER_FRAME = (288.36e6 + 10.23e6) / 1.1e6
 
 
 def measured_peaks():
