@@ -1,7 +1,7 @@
 """The paper's own enhanced-NMS layout on the GPU decoder, for comparison with its
 printed error rates (Sec. III-B, Sec. IV, Fig. 2).
 
-Layout: P = 9 automorphisms per frame -- three cyclic shifts spaced n/3 apart, each
+Layout: P = 9 automorphisms per frame -- three cyclic shifts spaced d_p apart, each
 applied to y, to the interleaved word (z[u] = y[2u mod n]) and to the Frobenius word
 (z[u] = y[2^-1 u mod n]), with one random offset per frame; I_m = 4 iterations for
 n = 63; the Table I matrix sizes (BCH(63,36): 122 rows, BCH(63,45): 33 rows); one
@@ -11,7 +11,16 @@ for n = 63 and does not print it).
 In the library's map pi(i) = 2^j i + s with z[pi(i)] = y[i], the interleaved word is
 j = m - 1 (pi^-1(u) = 2u) and the Frobenius word is j = 1.
 
+The redundancy ladder (Sec. III-A): BCH(63,36) with H_o of M_o = 27 ... 316 rows, the
+same layout, alpha re-picked at 2.6 dB for every matrix and the FER taken at 3.5 dB,
+against the (beta, M_o, FER) sequence the paper prints.  The paper states that ladder
+without knowledge of the noise variance; min-sum is homogeneous in its input (every
+step -- magnitudes, minima, alpha scaling, sums, the merge -- scales with it), so the
+decisions do not depend on the LLR scale and the usual 2y/sigma^2 input gives the same
+FER.
+
     python -m paper_2412_20828_gb300.paper_layout --frames 1000000 --json out.json
+    python -m paper_2412_20828_gb300.paper_layout --ladder --frames 1000000
 """
 from __future__ import annotations
 
@@ -28,13 +37,19 @@ PRINTED = {
 }
 
 
+# redundancy ladder of BCH(63,36), Sec. III-A: (beta, M_o, FER at 3.5 dB), I_m = 4
+PRINTED_LADDER = {(63, 36): [(1, 27, 0.077), (5, 47, 0.051), (20, 122, 0.030), (50, 269, 0.027),
+                             (60, 316, 0.028)]}
+
+
 def paper_block(n: int, m: int, frames: int, frame0: int, seed: int) -> np.ndarray:
-    """[frames][9] packed (s | j << 8): shifts d_o + q n/3 (q = 0, 1, 2) of the
-    identity, interleave (j = m - 1) and Frobenius (j = 1) words; d_o uniform per frame
-    from a seeded generator (the block's only randomness)."""
-    rng = np.random.default_rng([seed, frame0])
-    d_o = rng.integers(0, n, size=frames)
+    """[frames][9] packed (s | j << 8): shifts d_o + q d_p (q = 0, 1, 2; d_p = 21 for
+    n = 63, 42 for n = 127) of the identity, interleave (j = m - 1) and Frobenius (j = 1)
+    words; the offset d_o is uniform in [0, d_p) per frame from a seeded generator (the
+    block's only randomness)."""
     step = n // 3
+    rng = np.random.default_rng([seed, frame0])
+    d_o = rng.integers(0, step, size=frames)
     out = np.empty((frames, 9), np.uint16)
     col = 0
     for j in (0, m - 1, 1):
@@ -93,12 +108,85 @@ def run(frames=1_000_000, alphas=(0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95, 1.
     return res
 
 
+def run_ladder(frames=1_000_000, alphas=tuple(round(0.3 + 0.05 * i, 2) for i in range(15)),
+               chunk=1 << 19, seed=0x2412, tune_frames=200_000, log=sys.stderr):
+    """FER at 3.5 dB of the paper layout per H_o size of the printed ladder, with alpha
+    picked by FER at 2.6 dB for each size (0.3 ... 1.0: larger matrices send more
+    check messages to each bit and want smaller factors), and the device time of the
+    NMS launches."""
+    import os
+    import torch
+    from . import bchdec as B
+    B.load()
+    res = {"frames_per_point": frames, "iters": 4, "P": 9, "codes": {}}
+    for (n, k), ladder in PRINTED_LADDER.items():
+        m = 6
+        ld = 64
+        Fc = min(chunk, frames)
+        llr = torch.empty((Fc, ld), dtype=torch.float32, device="cuda")
+        cw = torch.empty((Fc, 1), dtype=torch.int64, device="cuda")
+        hard = torch.empty((Fc, 1), dtype=torch.int64, device="cuda")
+        its = torch.empty(Fc, dtype=torch.uint8, device="cuda")
+        flg = torch.empty(Fc, dtype=torch.uint8, device="cuda")
+        rows_out = []
+        for beta, mo, fer_p in ladder:
+            # matrices above 126 rows run on the precompiled kernel: the specialised one
+            # computes the same decisions but takes a minute to compile at that size
+            prev = os.environ.get("BCHDEC_NMS_KERNEL")
+            if mo > 126:
+                os.environ["BCHDEC_NMS_KERNEL"] = "generic"
+            try:
+                code = B.Code(n, k, m_rows=mo)
+                ws = B.workspace(code, B.params(4, 0.7, n_autos=9), Fc)
+                kinfo = code.kernel_info(B.MSG_FP32, 9)
+                stream = torch.cuda.current_stream()
+
+                def decode(ebn0, alpha, total, base):
+                    ctr = torch.zeros(8, dtype=torch.int64, device="cuda")
+                    p = B.params(4, alpha, n_autos=9)
+                    dev_ms = 0.0
+                    for f0 in range(0, total, Fc):
+                        F = min(Fc, total - f0)
+                        B.gen_frames(code, ebn0, ebn0, seed, base + f0, llr[:F], cw[:F])
+                        aut = torch.from_numpy(paper_block(n, m, F, base + f0, seed).view(np.int16)).cuda()
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        B.nms_decode(code, p, llr[:F], aut, hard[:F], its[:F], flg[:F], ws=ws)
+                        b.record(stream)
+                        B.count_errors(n, hard[:F], cw[:F], its[:F], flg[:F], ctr)
+                        b.synchronize()
+                        dev_ms += a.elapsed_time(b)
+                    c = ctr.cpu().numpy()
+                    return {"frames": int(c[0]), "fer": float(c[1] / c[0]), "frame_errors": int(c[1]),
+                            "ber": float(c[2] / (c[0] * n)), "avg_iters": float(c[5] / c[0]),
+                            "frames_per_s": float(c[0] / (dev_ms / 1e3))}
+
+                sweep = {a: decode(2.6, a, min(frames, tune_frames), 10**9) for a in alphas}
+                best = min(alphas, key=lambda a: sweep[a]["fer"])
+                r = decode(3.5, best, frames, 37 * 10**9)
+                r.update({"beta_paper": beta, "M_o": code.rows, "edges": code.edges, "alpha": best,
+                          "paper_fer": fer_p, "ratio": r["fer"] / fer_p, "kernel": kinfo,
+                          "alpha_sweep_2p6dB_fer": {str(a): sweep[a]["fer"] for a in alphas}})
+                rows_out.append(r)
+                print(f"({n},{k}) M_o={code.rows} alpha={best} FER@3.5dB={r['fer']:.4f} "
+                      f"(paper {fer_p}) {r['frames_per_s'] / 1e6:.1f} M frames/s [{kinfo}]", file=log)
+                code.close()
+            finally:
+                if prev is None:
+                    os.environ.pop("BCHDEC_NMS_KERNEL", None)
+                else:
+                    os.environ["BCHDEC_NMS_KERNEL"] = prev
+        res["codes"][f"({n},{k})"] = rows_out
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--frames", type=int, default=1_000_000)
     ap.add_argument("--json", default=None)
+    ap.add_argument("--ladder", action="store_true", help="the BCH(63,36) redundancy ladder")
     a = ap.parse_args(argv)
-    res = run(a.frames)
+    res = run_ladder(a.frames) if a.ladder else run(a.frames)
     print(json.dumps(res, indent=1))
     if a.json:
         with open(a.json, "w") as f:
