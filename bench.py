@@ -207,8 +207,12 @@ def run_serving(B, torch, dev, seconds, rate):
                         it, fl)
     torch.cuda.synchronize()
     progress("serving: kernels ready")
+    # the server compiles its serving kernel (every code's rows specialised) here,
+    # before any timed stream
     srv = B.Server(codes, stds, ITERS, ALPHA, n_autos=P_AUTOS, osd_order=OSD_ORDER,
                    budget_bytes=16 << 30, max_requests=8192, max_frames_per_request=4096)
+    server_kernel = srv.kernel_info()
+    progress(f"serving: server kernel {server_kernel}")
     # warm-up: a short stream
     B.serve_bench(srv, codes, stds, pools, rate, 0.5, seed=11)
     progress("serving: server at the configured rate")
@@ -234,7 +238,7 @@ def run_serving(B, torch, dev, seconds, rate):
                                    batch_us=1000, batch_frames=65536)
     return {"workload": f"Poisson {rate:.0f} req/s, 1-4096 frames log-uniform, codes "
                         "(63,36),(63,45),(127,64),(127,99), Eb/N0 U[1,6] dB, hybrid NMS(12,P=3)+OSD(2)",
-            "seconds": seconds, "server": res, "static_batching": stat,
+            "seconds": seconds, "server_kernel": server_kernel, "server": res, "static_batching": stat,
             "below_saturation": {"rate_rps": sub, "server": res_sub, "static_batching": stat_sub},
             "static_batching_plain_nms": plain,
             "server_stats": stats}

@@ -323,6 +323,21 @@ bch_status bch_server_poll(bch_server *srv, uint64_t *done_ids, int max_ids, int
 bch_status bch_server_fetch(bch_server *srv, uint64_t request_id, uint64_t *hard,
                             uint8_t *iters, uint8_t *flags);
 bch_status bch_server_get_stats(bch_server *srv, bch_server_stats *out);
+/* Names the serving kernel the server runs: "jit" -- compiled at server creation
+ * (NVRTC) with every code's rows as straight-line code, one automorphism copy per code
+ * as in the batch decoder's specialised kernel, cached in the process and on disk
+ * like it -- or "generic: <reason>" -- the precompiled kernel reading the rows from the
+ * codes' device tables.  BCHDEC_NMS_KERNEL (read at bch_server_create) selects as for
+ * the batch decoders: generic, jit (creation fails if the compile fails) or auto
+ * (default).  Both compute the same results, equal to the batch hybrid decoder's.
+ * buf: caller-owned, capacity bytes, always NUL-terminated. */
+bch_status bch_server_kernel_info(bch_server *srv, char *buf, size_t capacity);
+/* Compiles, for sm_103a with ptxas reporting on, the serving kernel a server of the
+ * optimized matrices of BCH(n[i], k[i]) (i < n_codes <= 8, default row counts, matrix
+ * seed `seed`) would run, without loading it: no GPU is needed.  log as in
+ * bch_nms_jit_check.  No counterpart in the paper: a build aid. */
+bch_status bch_serve_jit_check(int n_codes, const int *n, const int *k, uint64_t seed, char *log,
+                               size_t capacity);
 /* Stops the kernel (at its next chunk boundary) and frees everything. */
 void bch_server_destroy(bch_server *srv);
 

@@ -30,7 +30,8 @@ EXPORTS = (
     "bch_compact_failed", "bch_count_errors", "bch_nms_forward_train", "bch_nms_backward", "bch_bce_loss",
     "bch_train_alpha", "bch_decoder_create", "bch_decoder_run_host", "bch_decoder_destroy",
     "bch_server_create", "bch_server_submit", "bch_server_poll", "bch_server_fetch",
-    "bch_server_get_stats", "bch_server_destroy", "bch_serve_bench",
+    "bch_server_get_stats", "bch_server_kernel_info", "bch_serve_jit_check", "bch_server_destroy",
+    "bch_serve_bench",
     "bch_status_str", "bch_last_error", "bch_version",
 )
 
@@ -134,6 +135,8 @@ def load():
             "bch_server_poll": (st, [P, P, i, C.POINTER(i), i]),
             "bch_server_fetch": (st, [P, u64, P, P, P]),
             "bch_server_get_stats": (st, [P, C.POINTER(ServerStats)]),
+            "bch_server_kernel_info": (st, [P, C.c_char_p, sz]),
+            "bch_serve_jit_check": (st, [i, C.POINTER(C.c_int), C.POINTER(C.c_int), u64, C.c_char_p, sz]),
             "bch_server_destroy": (None, [P]),
             "bch_serve_bench": (st, [P, C.POINTER(ServeBenchConfig), C.POINTER(ServeBenchResult)]),
             "bch_status_str": (C.c_char_p, [i]),
@@ -248,6 +251,19 @@ def nms_jit_check(n, k, msg=MSG_FP32, m_rows=0, seed=0x2412_20828) -> str:
     rc = load().bch_nms_jit_check(n, k, m_rows, seed, None, msg, buf, 1 << 16)
     if rc != OK:
         raise BchError(rc, "bch_nms_jit_check",
+                       buf.value.decode(errors="replace") or load().bch_last_error().decode())
+    return buf.value.decode(errors="replace")
+
+
+def serve_jit_check(codes, seed=0x2412_20828) -> str:
+    """Compiles the serving kernel specialised to the optimized matrices of the codes
+    [(n, k), ...] (no GPU needed); returns the compiler report or raises BchError."""
+    nn = (C.c_int * len(codes))(*[n for n, _ in codes])
+    kk = (C.c_int * len(codes))(*[k for _, k in codes])
+    buf = C.create_string_buffer(1 << 16)
+    rc = load().bch_serve_jit_check(len(codes), nn, kk, seed, buf, 1 << 16)
+    if rc != OK:
+        raise BchError(rc, "bch_serve_jit_check",
                        buf.value.decode(errors="replace") or load().bch_last_error().decode())
     return buf.value.decode(errors="replace")
 
@@ -466,6 +482,12 @@ class Server:
         _check(load().bch_server_fetch(self._h, rid, _ptr(hard), _ptr(it), _ptr(fl)),
                "bch_server_fetch")
         return hard.view(np.int64), it, fl
+
+    def kernel_info(self) -> str:
+        """"jit" (serving kernel specialised to the codes) or "generic: <reason>"."""
+        buf = C.create_string_buffer(4096)
+        _check(load().bch_server_kernel_info(self._h, buf, 4096), "bch_server_kernel_info")
+        return buf.value.decode()
 
     def stats(self):
         st = ServerStats()

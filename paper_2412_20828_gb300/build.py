@@ -43,7 +43,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     gen = os.path.join(OUT, "gen_device_text.cpp")
     with open(gen, "w") as f:
         f.write("namespace bchlib {\n")
-        for sym, name in (("kDevTypesText", "bch_devtypes.h"), ("kNmsDeviceText", "nms_device.cuh")):
+        for sym, name in (("kDevTypesText", "bch_devtypes.h"), ("kNmsDeviceText", "nms_device.cuh"),
+                          ("kAutosDeviceText", "autos_device.cuh"), ("kOsdDeviceText", "osd_device.cuh"),
+                          ("kServeDeviceText", "serve_device.cuh")):
             with open(os.path.join(CSRC, name)) as g:
                 text = g.read()
             assert ")__BCHTEXT__" not in text

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -17,6 +18,7 @@ using namespace bchlib;
 namespace bchlib {
 cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err);
 bool jit_compile_check(const bch_code *c, int msg, std::string *log);
+bool jit_serve_compile_check(const bch_code *const *codes, int n_codes, std::string *log);
 int jit_block_size(int n);
 int jit_scratch_words(int n);
 size_t nms_table_bytes_host(const DevCode &dc);
@@ -390,6 +392,24 @@ bch_status bch_nms_jit_check(int n, int k, int m_rows, uint64_t seed, const bch_
   const bool ok = jit_compile_check(&c, msg, &text);
   std::snprintf(log, capacity, "%s", text.c_str());
   return ok ? BCH_OK : fail(BCH_ECUDA, "NVRTC compile failed");
+}
+
+bch_status bch_serve_jit_check(int n_codes, const int *n, const int *k, uint64_t seed, char *log,
+                               size_t capacity) {
+  if (!log || capacity == 0 || !n || !k || n_codes < 1 || n_codes > 8)
+    return fail(BCH_EINVAL, "bad argument");
+  log[0] = 0;
+  std::unique_ptr<bch_code[]> cs(new bch_code[size_t(n_codes)]);
+  std::vector<const bch_code *> ptrs;
+  for (int i = 0; i < n_codes; i++) {
+    bch_status st = build_host(n[i], k[i], BCH_PCM_OPTIMIZED, 0, seed, nullptr, &cs[size_t(i)]);
+    if (st != BCH_OK) return st;
+    ptrs.push_back(&cs[size_t(i)]);
+  }
+  std::string text;
+  const bool ok = jit_serve_compile_check(ptrs.data(), n_codes, &text);
+  std::snprintf(log, capacity, "%s", text.c_str());
+  return ok ? BCH_OK : fail(BCH_ECUDA, "serving kernel compile failed");
 }
 
 bch_status bch_code_info(const bch_code *c, int *n, int *k, int *rows, int *edges, int *max_w) {

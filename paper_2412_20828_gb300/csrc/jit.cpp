@@ -36,6 +36,9 @@ namespace bchlib {
 
 extern const char kDevTypesText[];
 extern const char kNmsDeviceText[];
+extern const char kAutosDeviceText[];
+extern const char kOsdDeviceText[];
+extern const char kServeDeviceText[];
 
 namespace {
 
@@ -190,34 +193,38 @@ int jit_min_blocks(int n) {
 }
 int jit_scratch_words(int n) { return n <= 63 ? 0 : n; }
 
-std::string jit_source(const bch_code *c, int msg) {
-  const int n = c->alg.n, m = c->alg.m;
-  const int tpb = jit_block_size(n);
-  const int scratch = jit_scratch_words(n);
-  const int nw = (n + 31) / 32;
-  std::ostringstream o;
+// Common prologue of the generated sources: fixed-width types, the embedded device
+// headers, the three-input minimum and the row macros of one storage format.
+static void emit_prologue(std::ostringstream &o, int msg, bool serving) {
   o << "typedef unsigned int uint32_t;\ntypedef int int32_t;\ntypedef unsigned short uint16_t;\n"
        "typedef unsigned char uint8_t;\ntypedef signed char int8_t;\n"
        "typedef unsigned long long uint64_t;\ntypedef unsigned long long uintptr_t;\n"
        "#define FLT_MAX 3.402823466e+38f\n#include <cuda_fp16.h>\n";
   o << kDevTypesText << "\n" << kNmsDeviceText << "\n";
+  if (serving) o << kAutosDeviceText << "\n" << kOsdDeviceText << "\n" << kServeDeviceText << "\n";
   o << "namespace bchlib {\n"
     << "__device__ __forceinline__ float bch_min3f(float a, float b, float c) {\n"
     << "  float d;\n  asm(\"min.f32 %0, %1, %2, %3;\" : \"=f\"(d) : \"f\"(a), \"f\"(b), \"f\"(c));\n"
     << "  return d;\n}\n"
     << row_macros(msg);
+}
+
+// The statements of one automorphism copy of code c: gather z_p from the frame's y
+// column (element stride `stride`), the rows as straight-line code, scatter into the
+// accumulator column.  They use y, acc, scr, jr, sp and alpha; with `scratch` the row
+// sums live in the scratch column (same stride), else in registers.
+static void emit_copy_body(std::ostringstream &o, const bch_code *c, int msg, int stride, bool scratch) {
+  const int n = c->alg.n, m = c->alg.m;
+  const int nw = (n + 31) / 32;
+  o << "#undef BCH_SV\n";
   if (scratch)
-    o << "#define BCH_SV(u) scr[(u) * " << tpb << "]\n";
+    o << "#define BCH_SV(u) scr[(u) * " << stride << "]\n";
   else
     o << "#define BCH_SV(u) S[u]\n";
-  o << "struct JitCopy {\n  static constexpr int kScratch = " << scratch << ";\n"
-    << "  __device__ __forceinline__ void operator()(const SmemTables &, int, uint32_t, uint32_t,\n"
-    << "      StoreT<" << msg << ">::Y *y, StoreT<" << msg << ">::A *acc, StoreT<" << msg
-    << ">::A *scr, uint32_t jr, uint32_t sp, uint32_t, float alpha) const {\n"
-    << "    BCH_VT z[" << n << "];\n"
+  o << "    BCH_VT z[" << n << "];\n"
     << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) {\n"
     << "      const uint32_t i = addmod(bfe32(uint32_t(u) | (uint32_t(u) << " << m << "), jr, " << m
-    << "), sp, " << n << ");\n      z[u] = ld_y(y + i * " << tpb << ");\n    }\n";
+    << "), sp, " << n << ");\n      z[u] = ld_y(y + i * " << stride << ");\n    }\n";
   if (scratch)
     o << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) BCH_SV(u) = 0;\n";
   else
@@ -272,12 +279,70 @@ std::string jit_source(const bch_code *c, int msg) {
   }
   o << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) {\n"
     << "      const uint32_t i = addmod(bfe32(uint32_t(u) | (uint32_t(u) << " << m << "), jr, " << m
-    << "), sp, " << n << ");\n      acc[i * " << tpb << "] += BCH_FIN(u);\n    }\n  }\n};\n}  // namespace bchlib\n";
+    << "), sp, " << n << ");\n      acc[i * " << stride << "] += BCH_FIN(u);\n    }\n";
+}
+
+// The batch kernel's copy functor `name` (columns of stride `stride`).
+static void emit_copy(std::ostringstream &o, const bch_code *c, int msg, const std::string &name, int stride,
+                      bool scratch) {
+  o << "struct " << name << " {\n  static constexpr int kScratch = " << (scratch ? c->alg.n : 0) << ";\n"
+    << "  __device__ __forceinline__ void operator()(const SmemTables &, int, uint32_t, uint32_t,\n"
+    << "      StoreT<" << msg << ">::Y *y, StoreT<" << msg << ">::A *acc, StoreT<" << msg
+    << ">::A *scr, uint32_t jr, uint32_t sp, uint32_t, float alpha) const {\n";
+  emit_copy_body(o, c, msg, stride, scratch);
+  o << "  }\n};\n";
+}
+
+// The serving kernel's copy of code c (FP32) as a separate function, so that the
+// compiler optimises each code's rows on their own: the lane's columns (stride 32)
+// are found from the dynamic shared-memory base, in the serving layout (accumulator,
+// y, scratch).
+static void emit_serve_copy(std::ostringstream &o, const bch_code *c, const std::string &name, bool scratch) {
+  o << "__device__ __noinline__ void " << name << "(uint32_t jr, uint32_t sp, float alpha) {\n"
+    << "  extern __shared__ __align__(16) unsigned char smem[];\n"
+    << "  float *acc = reinterpret_cast<float *>(smem) + lane_id();\n"
+    << "  float *y = acc + 128 * 32;\n  float *scr = y + 128 * 32;\n  (void)scr;\n";
+  emit_copy_body(o, c, 0, 32, scratch);
+  o << "}\n";
+}
+
+std::string jit_source(const bch_code *c, int msg) {
+  const int n = c->alg.n;
+  const int tpb = jit_block_size(n);
+  const int nw = (n + 31) / 32;
+  std::ostringstream o;
+  emit_prologue(o, msg, false);
+  emit_copy(o, c, msg, "JitCopy", tpb, jit_scratch_words(n) > 0);
+  o << "}  // namespace bchlib\n";
   o << "extern \"C\" __global__ void __launch_bounds__(" << tpb << ", " << jit_min_blocks(n)
     << ") bch_nms_jit(const bchlib::NmsArgs a) {\n"
     << "  extern __shared__ __align__(16) unsigned char smem[];\n"
     << "  bchlib::nms_persistent<" << msg << ", " << nw << ", " << (jit_lockstep(n) ? "true" : "false")
     << ", " << tpb << ">(a, smem, bchlib::JitCopy());\n}\n";
+  return o.str();
+}
+
+// The serving kernel specialised to a server's codes (FP32 messages): one copy functor
+// per code on columns of stride 32 (one warp per block), row sums in registers for
+// n <= 63 and in the lane's scratch column for n = 127, dispatched on the warp's code.
+std::string jit_serve_source(const bch_code *const *codes, int n_codes) {
+  std::ostringstream o;
+  emit_prologue(o, 0, true);
+  for (int i = 0; i < n_codes; i++)
+    emit_serve_copy(o, codes[i], "srv_copy_" + std::to_string(i), codes[i]->alg.n > 63);
+  o << "struct SrvJitCopies {\n"
+    << "  __device__ __forceinline__ void operator()(int code, const SrvCode &, int P, float *, float *,\n"
+    << "      float *, const uint32_t *ctx, float alpha) const {\n"
+    << "    switch (code) {\n";
+  for (int i = 0; i < n_codes; i++)
+    o << "      case " << i << ":\n        for (int p = 0; p < P; p++) {\n"
+      << "          const uint32_t cx = ctx[p * 32];\n"
+      << "          srv_copy_" << i << "(cx & 0xffu, cx >> 8, alpha);\n"
+      << "        }\n        break;\n";
+  o << "      default: break;\n    }\n  }\n};\n}  // namespace bchlib\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(32) bch_serve_jit(const bchlib::SrvArgs a) {\n"
+    << "  extern __shared__ __align__(16) unsigned char smem[];\n"
+    << "  bchlib::serve_loop(a, smem, bchlib::SrvJitCopies());\n}\n";
   return o.str();
 }
 
@@ -381,8 +446,9 @@ cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
   return k;
 }
 
-cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err) {
-  const std::string src = jit_source(c, msg);
+// Compiles `src` (or loads it from the on-disk cache) and returns its kernel `entry`;
+// cached in the process per source text.  On failure returns nullptr and sets *err.
+static cudaKernel_t compile_source(const std::string &src, const char *entry, std::string *err) {
   std::shared_ptr<Compiled> cp;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -401,7 +467,7 @@ cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err
   std::vector<char> cached;
   if (!cache_file.empty() && read_file(cache_file, &cached) &&
       cudaLibraryLoadData(&cp->lib, cached.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) == cudaSuccess &&
-      cudaLibraryGetKernel(&cp->kernel, cp->lib, "bch_nms_jit") == cudaSuccess) {
+      cudaLibraryGetKernel(&cp->kernel, cp->lib, entry) == cudaSuccess) {
     // loaded a kernel compiled earlier from the same source
   } else if (!api.ok) {
     cp->kernel = nullptr;
@@ -409,7 +475,8 @@ cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err
   } else {
     cp->kernel = nullptr;
     nvrtcProgram prog = nullptr;
-    if (api.create(&prog, src.c_str(), "bch_nms_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    if (api.create(&prog, src.c_str(), (std::string(entry) + ".cu").c_str(), 0, nullptr, nullptr) !=
+        NVRTC_SUCCESS) {
       cp->err = "nvrtcCreateProgram failed";
     } else {
       const nvrtcResult r = api.compile(prog, 4, opts);
@@ -426,7 +493,7 @@ cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err
         api.cubin(prog, cubin.data());
         cudaError_t e = cudaLibraryLoadData(&cp->lib, cubin.data(), nullptr, nullptr, 0, nullptr,
                                             nullptr, 0);
-        if (e == cudaSuccess) e = cudaLibraryGetKernel(&cp->kernel, cp->lib, "bch_nms_jit");
+        if (e == cudaSuccess) e = cudaLibraryGetKernel(&cp->kernel, cp->lib, entry);
         if (e != cudaSuccess) {
           cp->kernel = nullptr;
           cp->err = std::string("loading the compiled kernel: ") + cudaGetErrorString(e);
@@ -445,15 +512,32 @@ cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err
   return cp->kernel;
 }
 
+cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err) {
+  return compile_source(jit_source(c, msg), "bch_nms_jit", err);
+}
+
+cudaKernel_t jit_serve_kernel(const bch_code *const *codes, int n_codes, std::string *err) {
+  return compile_source(jit_serve_source(codes, n_codes), "bch_serve_jit", err);
+}
+
 // Compiles the specialised source with ptxas reporting on; no GPU is needed.  Returns
 // false with *log holding the compiler output on failure.
+static bool compile_check_source(const std::string &src, const char *entry, std::string *log);
+
 bool jit_compile_check(const bch_code *c, int msg, std::string *log) {
+  return compile_check_source(jit_source(c, msg), "bch_nms_jit", log);
+}
+
+bool jit_serve_compile_check(const bch_code *const *codes, int n_codes, std::string *log) {
+  return compile_check_source(jit_serve_source(codes, n_codes), "bch_serve_jit", log);
+}
+
+static bool compile_check_source(const std::string &src, const char *entry, std::string *log) {
   NvrtcApi &api = nvrtc();
   if (!api.ok) {
     *log = api.err;
     return false;
   }
-  const std::string src = jit_source(c, msg);
   // BCHDEC_JIT_DUMP=<file>: also write the generated source there (a debugging aid)
   if (const char *dump = std::getenv("BCHDEC_JIT_DUMP")) {
     if (FILE *fp = std::fopen(dump, "w")) {
@@ -462,7 +546,7 @@ bool jit_compile_check(const bch_code *c, int msg, std::string *log) {
     }
   }
   nvrtcProgram prog = nullptr;
-  if (api.create(&prog, src.c_str(), "bch_nms_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+  if (api.create(&prog, src.c_str(), (std::string(entry) + ".cu").c_str(), 0, nullptr, nullptr) != NVRTC_SUCCESS) {
     *log = "nvrtcCreateProgram failed";
     return false;
   }

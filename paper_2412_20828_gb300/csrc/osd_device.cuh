@@ -18,7 +18,9 @@
 //    the lexicographic minimum of (score, enumeration index): the result equals a
 //    sequential scan that keeps the first minimum.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include "nms_device.cuh"
+#endif
 
 namespace bchlib {
 

@@ -77,3 +77,17 @@ def test_specialised_kernel_compiles_without_gpu(msg):
     (NVRTC, no GPU) in every message format."""
     report = B.nms_jit_check(63, 45, msg)
     assert "registers" in report
+
+
+def test_serving_kernel_compiles_without_gpu():
+    """The serving kernel specialised to a server's codes compiles for sm_103a (NVRTC,
+    no GPU): one separate copy function per code, none of them spilling for n = 63."""
+    report = B.serve_jit_check([(63, 45), (63, 36)])
+    assert "bch_serve_jit" in report
+    assert "srv_copy_0" in report and "srv_copy_1" in report
+    for line in report.splitlines():
+        if "srv_copy" in line:
+            props = report.splitlines()[report.splitlines().index(line) + 1]
+            assert "0 bytes spill stores" in props
+    with pytest.raises(B.BchError):
+        B.serve_jit_check([(63, 45)] * 9)  # at most 8 codes

@@ -1,6 +1,7 @@
 """Continuous-batching server: results are the same alone and in a mixed stream, equal
-to the batch hybrid decoder on the same frames (same precompiled arithmetic), and the
-admission honours the HBM budget (queueing, never dropping)."""
+to the batch hybrid decoder on the same frames, on both serving kernels (the one
+specialised to the server's codes and the precompiled one), and the admission honours
+the HBM budget (queueing, never dropping)."""
 import numpy as np
 import pytest
 
@@ -24,7 +25,8 @@ def setup():
 
 
 def _batch_reference(torch, monkeypatch, code, std, llr, seed, frame0):
-    # the batch hybrid decoder on the precompiled kernel (the server's arithmetic)
+    # the batch hybrid decoder on the precompiled kernel (bit-identical to the
+    # specialised one: test_jit_and_generic_kernels_agree)
     monkeypatch.setenv("BCHDEC_NMS_KERNEL", "generic")
     F, ld = llr.shape
     aut = torch.zeros((F, 3), dtype=torch.int16, device="cuda")
@@ -48,10 +50,15 @@ def _drain(srv, want):
     raise AssertionError("server did not complete the requests")
 
 
-def test_results_alone_and_in_mix_match_batch_decoder(setup, monkeypatch):
+@pytest.mark.parametrize("kernel", ["jit", "generic"])
+def test_results_alone_and_in_mix_match_batch_decoder(setup, monkeypatch, kernel):
     torch, codes, stds = setup
+    monkeypatch.setenv("BCHDEC_NMS_KERNEL", kernel)
     srv = B.Server(codes, stds, 12, 0.78, budget_bytes=1 << 30, max_requests=256)
+    monkeypatch.delenv("BCHDEC_NMS_KERNEL")
     try:
+        info = srv.kernel_info()
+        assert info == "jit" if kernel == "jit" else info.startswith("generic")
         reqs = []
         for i, (n, k) in enumerate(CODES):
             for j, (F, e) in enumerate([(37, 2.0), (300, 3.0), (1, 4.0)]):
