@@ -192,6 +192,36 @@ void arena_free(bch_server *s, size_t off, size_t bytes) {
   }
 }
 
+// Waits for stream `st` for at most `limit_s` seconds (no unbounded host wait on the
+// persistent kernel or the copies): BCH_ETIMEOUT, with the server's state in the
+// message, when it is still busy.
+bch_status wait_stream(bch_server *s, cudaStream_t st, double limit_s, const char *what) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) return BCH_OK;
+    if (e != cudaErrorNotReady) return fail(BCH_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s) {
+      // device counters, read on the legacy stream (the server's streams do not
+      // block on it)
+      SrvDev dv{};
+      cudaMemcpy(&dv, s->dv, sizeof(dv), cudaMemcpyDeviceToHost);
+      char msg[320];
+      std::snprintf(msg, sizeof(msg),
+                    "%s: still busy after %.0f s (running %u, live warps %u, completions %u, published open %lld, "
+                    "pending %zu)",
+                    what, limit_s, unsigned(s->sh->running), dv.live, dv.comp_tail, s->published_open,
+                    s->pending.size());
+      return fail(BCH_ETIMEOUT, msg);
+    }
+    // copies finish in microseconds: yield first, sleep only on long waits
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() < 1e-3)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
 bch_status launch_server_kernel(bch_server *s) {
   s->sh->running = 1;
   s->args.dv = s->dv;
@@ -209,8 +239,11 @@ bch_status launch_server_kernel(bch_server *s) {
 
 bch_status ensure_running(bch_server *s) {
   if (s->published_open > 0 && !s->sh->running) {
-    cudaStreamSynchronize(s->kst);  // a previous instance that exited idle has finished
-    bch_status st = launch_server_kernel(s);
+    // a previous instance that exited idle has finished (its last warp cleared the
+    // flag on the way out)
+    bch_status st = wait_stream(s, s->kst, 30.0, "serve kernel exit");
+    if (st != BCH_OK) return st;
+    st = launch_server_kernel(s);
     if (st != BCH_OK) return st;
     s->stats.kernel_launches++;
   }
@@ -570,8 +603,9 @@ bch_status bch_server_fetch(bch_server *s, uint64_t id, uint64_t *hard, uint8_t 
   cudaError_t e = cudaMemcpyAsync(hard, base + L.hard, size_t(r.F) * W64 * 8, cudaMemcpyDefault, s->cst);
   if (e == cudaSuccess && iters) e = cudaMemcpyAsync(iters, base + L.iters, size_t(r.F), cudaMemcpyDefault, s->cst);
   if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, base + L.flags, size_t(r.F), cudaMemcpyDefault, s->cst);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->cst);
   if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("fetch: ") + cudaGetErrorString(e));
+  bch_status ws = wait_stream(s, s->cst, 30.0, "fetch copies");
+  if (ws != BCH_OK) return ws;
   arena_free(s, r.off, r.bytes);
   s->stats.bytes_in_use -= r.bytes;
   s->free_slots.push_back(r.slot);
@@ -598,8 +632,11 @@ void bch_server_destroy(bch_server *s) {
   if (!s) return;
   s->sh->stop = 1;
   std::atomic_thread_fence(std::memory_order_seq_cst);
-  cudaStreamSynchronize(s->kst);
-  cudaStreamSynchronize(s->cst);
+  // the kernel leaves at its next iteration; if it does not, its memory stays
+  // allocated (freeing it under a running kernel would fault) and the error is kept
+  if (wait_stream(s, s->kst, 30.0, "serve kernel stop") != BCH_OK ||
+      wait_stream(s, s->cst, 30.0, "server copies") != BCH_OK)
+    return;
   cudaStreamDestroy(s->kst);
   cudaStreamDestroy(s->cst);
   cudaFreeHost(s->sh);

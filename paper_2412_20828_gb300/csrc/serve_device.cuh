@@ -207,7 +207,8 @@ __device__ __forceinline__ void serve_loop(const SrvArgs &a, unsigned char *smem
           const SrvSlot sl = load_slot(a.slots + slot);
           const float *src = sl.llr + size_t(f) * sl.ld;
           for (int i = 0; i < n; i++) {
-            y[i * 32 + lane] = src[i] + 0.0f;  // -0 -> +0
+            // past L1: the arena is rewritten by copies while the kernel runs
+            y[i * 32 + lane] = __ldcg(src + i) + 0.0f;  // -0 -> +0
             acc[i * 32 + lane] = 0.0f;
           }
           uint32_t va[9];
