@@ -206,10 +206,29 @@ __device__ __forceinline__ void serve_loop(const SrvArgs &a, unsigned char *smem
           // the host rewrites a slot between requests: read the descriptor past L1
           const SrvSlot sl = load_slot(a.slots + slot);
           const float *src = sl.llr + size_t(f) * sl.ld;
-          for (int i = 0; i < n; i++) {
-            // past L1: the arena is rewritten by copies while the kernel runs
-            y[i * 32 + lane] = __ldcg(src + i) + 0.0f;  // -0 -> +0
-            acc[i * 32 + lane] = 0.0f;
+          // loads past L1 (the arena is rewritten by copies while the kernel runs),
+          // 16 bytes at a time when the rows allow it: the (n + 3) / 4 vectors stay
+          // within a row because ld is a multiple of 4 and at least n
+          if ((sl.ld & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            const float4 *src4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll 4
+            for (int q = 0; q < (n + 3) / 4; q++) {
+              const float4 v = __ldcg(src4 + q);
+              const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int r = 0; r < 4; r++) {
+                const int i = 4 * q + r;
+                if (i < n) {
+                  y[i * 32 + lane] = vv[r] + 0.0f;  // -0 -> +0
+                  acc[i * 32 + lane] = 0.0f;
+                }
+              }
+            }
+          } else {
+            for (int i = 0; i < n; i++) {
+              y[i * 32 + lane] = __ldcg(src + i) + 0.0f;
+              acc[i * 32 + lane] = 0.0f;
+            }
           }
           uint32_t va[9];
           draw_frame_autos(n, cd.ord, a.P, sl.seed, sl.frame0 + uint64_t(f), va);
