@@ -41,6 +41,16 @@ def test_pcm_bit_exact_with_oracle(nk):
     assert np.array_equal(B.build_pcm_host(n, k), O.build_ho(n, k))
 
 
+@pytest.mark.parametrize("n,k,m_rows", [(63, 36, 27), (63, 36, 47), (63, 36, 122), (63, 36, 269), (63, 36, 316),
+                                         (63, 45, 33), (63, 45, 78), (127, 64, 72), (127, 78, 57), (127, 99, 33)])
+def test_pcm_paper_sizes_bit_exact(n, k, m_rows):
+    # the row counts of Table I and of the redundancy ladder of Sec. III-A, including
+    # the padded matrices (more rows than the search's distinct classes)
+    a = B.build_pcm_host(n, k, m_rows=m_rows)
+    assert a.shape == (m_rows, n)
+    assert np.array_equal(a, O.build_ho(n, k, m_rows=m_rows))
+
+
 @pytest.mark.parametrize("seed,m_rows,q,sa", [(1, 0, 4, 20000), (99, 40, 2, 5000), (7, 60, 1, 300)])
 def test_pcm_options_bit_exact(seed, m_rows, q, sa):
     a = B.build_pcm_host(63, 45, m_rows=m_rows, seed=seed, q_rounds=q, sa_steps=sa)
