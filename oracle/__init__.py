@@ -337,6 +337,29 @@ def hybrid(Ho, Hstd, llr, autos, iters, alpha, order=2, threads=1):
     return r
 
 
+def hybrid_nms_reliability(Ho, Hstd, llr, autos, iters, alpha, order=2, threads=1):
+    """Hybrid decoder with the OSD fallback ranking and scoring positions by the NMS
+    output y of each failed frame instead of its channel LLR (the paper feeds OSD the
+    channel LLR, Sec. II-B; this is the alternative input).  y grows by about an order
+    of magnitude per iteration, past the OSD's integer weights floor(|L| 2^24) capped
+    at 2^40, so each failed frame's y is first scaled by the power of two that puts
+    max_i |y_i| in [2^15, 2^16) (exact) and rounded to FP32, the OSD's input format.
+    Decisions do not depend on the scale: min-sum is homogeneous in its input and the
+    scaling is per frame."""
+    r = nms_enhanced(Ho, llr, autos, iters, alpha, early_stop=True, threads=threads)
+    fail = np.nonzero(r["converged"] == 0)[0]
+    final = r["hard"].copy()
+    if fail.size:
+        y = r["y"][fail]
+        _, ex = np.frexp(np.max(np.abs(y), axis=1))  # max |y| = m 2^ex, m in [0.5, 1)
+        ys = np.ldexp(y, (16 - ex)[:, None]).astype(np.float32)
+        cw, _ = osd(Hstd, ys, order, threads=threads)
+        final[fail] = cw
+    r["final"] = final
+    r["osd_frames"] = fail
+    return r
+
+
 def train_grad(Ho, llr, autos, iters, alpha, cw, return_margin=False):
     Ho = np.ascontiguousarray(Ho, np.uint8)
     M, n = Ho.shape

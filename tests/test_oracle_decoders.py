@@ -320,6 +320,39 @@ def test_osd2_close_to_ml_on_bch15_7():
     assert fer_o2 - fer_ml < 0.01
 
 
+def test_hybrid_on_nms_reliabilities_is_ml_on_them_for_bch15_7():
+    # With order k the OSD tries every word of the basis, so on BCH(15,7) it returns
+    # the maximum-likelihood word for whatever reliabilities it is given: here the NMS
+    # output y of the failed frames (ML is scale invariant, so y itself, unscaled,
+    # serves as the reference metric).
+    n, k = 15, 7
+    Ho = O.build_ho(n, k)
+    # 0 dB and 2 iterations leave about a sixth of the frames to the OSD
+    _, llr = _frames(n, k, 600, 0.0, 101)
+    aut = O.draw_autos(n, 3, 7, 0, 600)
+    r = O.hybrid_nms_reliability(Ho, O.std_h(n, k), llr, aut, 2, 0.8, order=k)
+    fail = r["osd_frames"]
+    assert fail.size > 50
+    nms = O.nms_enhanced(Ho, llr, aut, 2, 0.8)
+    ml_y = O.ml(n, k, nms["y"][fail].astype(np.float32))
+    assert np.array_equal(r["final"][fail], ml_y)
+    # and the input really is y: ML on the channel LLR differs on some of those frames
+    assert not np.array_equal(ml_y, O.ml(n, k, llr[fail]))
+
+
+def test_hybrid_on_nms_reliabilities_is_scale_free():
+    n, k = 63, 45
+    Ho, Hs = O.build_ho(n, k), O.std_h(n, k)
+    _, llr = _frames(n, k, 200, 2.0, 111)
+    aut = O.draw_autos(n, 3, 9, 0, 200)
+    a = O.hybrid_nms_reliability(Ho, Hs, llr, aut, 12, 0.78)
+    b = O.hybrid_nms_reliability(Ho, Hs, (llr * 8.0).astype(np.float32), aut, 12, 0.78)
+    assert a["osd_frames"].size > 10
+    assert np.array_equal(a["final"], b["final"])
+    # every output is a codeword
+    assert all(O.syndrome_weight(Hs, w) == 0 for w in a["final"])
+
+
 # ------------------------------------------------------------------ gradient
 def test_train_grad_matches_central_differences():
     n, k = 63, 45
