@@ -191,6 +191,7 @@ __device__ __forceinline__ void serve_loop(const SrvArgs &a, unsigned char *smem
       if (lane == 0) nseg = srv_claim(a, wc, __popc(need), seg);
       nseg = __shfl_sync(kFull, nseg, 0);
       __syncwarp();
+      const float *src = nullptr;  // the LLR row of this lane's new frame
       if (f < 0 && nseg > 0) {
         int r = __popc(need & ((1u << lane) - 1u));
         for (int q = 0; q < nseg; q++) {
@@ -205,31 +206,7 @@ __device__ __forceinline__ void serve_loop(const SrvArgs &a, unsigned char *smem
         if (f >= 0) {
           // the host rewrites a slot between requests: read the descriptor past L1
           const SrvSlot sl = load_slot(a.slots + slot);
-          const float *src = sl.llr + size_t(f) * sl.ld;
-          // loads past L1 (the arena is rewritten by copies while the kernel runs),
-          // 16 bytes at a time when the rows allow it: the (n + 3) / 4 vectors stay
-          // within a row because ld is a multiple of 4 and at least n
-          if ((sl.ld & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-            const float4 *src4 = reinterpret_cast<const float4 *>(src);
-#pragma unroll 4
-            for (int q = 0; q < (n + 3) / 4; q++) {
-              const float4 v = __ldcg(src4 + q);
-              const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-              for (int r = 0; r < 4; r++) {
-                const int i = 4 * q + r;
-                if (i < n) {
-                  y[i * 32 + lane] = vv[r] + 0.0f;  // -0 -> +0
-                  acc[i * 32 + lane] = 0.0f;
-                }
-              }
-            }
-          } else {
-            for (int i = 0; i < n; i++) {
-              y[i * 32 + lane] = __ldcg(src + i) + 0.0f;
-              acc[i * 32 + lane] = 0.0f;
-            }
-          }
+          src = sl.llr + size_t(f) * sl.ld;
           uint32_t va[9];
           draw_frame_autos(n, cd.ord, a.P, sl.seed, sl.frame0 + uint64_t(f), va);
           const uint32_t m = uint32_t(cd.dc.m);
@@ -240,6 +217,19 @@ __device__ __forceinline__ void serve_loop(const SrvArgs &a, unsigned char *smem
             ctx[p * 32 + lane] = j | ((rs ? uint32_t(n) - rs : 0u) << 8);
           }
           t = 0;
+        }
+      }
+      __syncwarp();
+      // the whole warp loads each new frame's row: coalesced reads (lane q takes
+      // elements q, q + 32, ...) past L1, since copies rewrite the arena while the
+      // kernel runs
+      for (unsigned fm = __ballot_sync(kFull, src != nullptr); fm; fm &= fm - 1) {
+        const int l = __ffs(fm) - 1;
+        const float *row = reinterpret_cast<const float *>(
+            __shfl_sync(kFull, reinterpret_cast<unsigned long long>(src), l));
+        for (int i = lane; i < n; i += 32) {
+          y[i * 32 + l] = __ldcg(row + i) + 0.0f;  // -0 -> +0
+          acc[i * 32 + l] = 0.0f;
         }
       }
       __syncwarp();
