@@ -279,22 +279,32 @@ __device__ __forceinline__ void serve_loop(const SrvArgs &a, unsigned char *smem
       osd_one_frame(S, n, cd.dc.k, cd.M, cd.std_cols, sl.llr + size_t(f_l) * sl.ld, a.order,
                     sl.hard + size_t(f_l) * W64, sl.flags + f_l);
     }
-    // ---- count finished frames; the frame that completes a request posts it
-    if (done) {
-      __threadfence();
-      const SrvSlot sl = load_slot(a.slots + slot);
-      const unsigned d = atomicAdd(&a.slots[slot].done, 1u) + 1u;
-      if (int(d) == sl.F) {
-        const unsigned ci = atomicAdd(&a.dv->comp_tail, 1u);
-        SrvComp *c = a.comp + (ci % unsigned(a.ring));
-        c->id = sl.id;
-        c->t_ns = globaltimer();
-        c->slot = unsigned(slot);
-        __threadfence_system();
-        *reinterpret_cast<volatile unsigned *>(&c->seq) = ci + 1;
+    // ---- count finished frames: per request, one of the lanes that finished frames
+    // of it adds them all to the request's done counter, and the add that completes
+    // the request posts it
+    const unsigned dmask = __ballot_sync(kFull, done);
+    if (dmask) {
+      if (done) __threadfence();  // this lane's result writes
+      __syncwarp();               // ... and every other lane's (the OSD's included)
+      if (done) {
+        const unsigned peers = __match_any_sync(dmask, slot);
+        if (lane == __ffs(peers) - 1) {
+          const SrvSlot sl = load_slot(a.slots + slot);
+          const unsigned cnt = unsigned(__popc(peers));
+          const unsigned d = atomicAdd(&a.slots[slot].done, cnt) + cnt;
+          if (int(d) == sl.F) {
+            const unsigned ci = atomicAdd(&a.dv->comp_tail, 1u);
+            SrvComp *c = a.comp + (ci % unsigned(a.ring));
+            c->id = sl.id;
+            c->t_ns = globaltimer();
+            c->slot = unsigned(slot);
+            __threadfence_system();
+            *reinterpret_cast<volatile unsigned *>(&c->seq) = ci + 1;
+          }
+        }
+        f = -1;
+        slot = -1;
       }
-      f = -1;
-      slot = -1;
     }
   }
   if (lane == 0) {
