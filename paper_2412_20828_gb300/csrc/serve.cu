@@ -8,12 +8,16 @@
 // code are published to that code's ring; claims are generation-checked CAS on a
 // per-request counter and may span requests), so lanes never wait for a chunk's
 // slowest frame.  A warp binds to one code while any lane has a frame and picks a
-// code with published work when all its lanes are idle.  Frames whose syndrome stays
-// nonzero get OSD from the whole warp; every finished frame is added to its request's
-// done counter and the frame that completes a request posts a completion record to a
-// ring in host-mapped memory.  Every wait is bounded: idle warps sleep and the kernel
-// exits after `idle_exit_us` without work (the host relaunches it), and a stop flag
-// ends it at the next iteration.
+// code with published work when all its lanes are idle.  New frames are loaded by
+// the whole warp with coalesced reads past L1.  Frames whose syndrome stays nonzero
+// get OSD from the whole warp; after a warp barrier the finished frames are added to
+// their requests' done counters (one atomic per request and warp), and the add that
+// completes a request posts a completion record to a ring in host-mapped memory.
+// Every wait is bounded: idle warps sleep and the kernel exits after `idle_exit_us`
+// without work (the host relaunches it), and a stop flag ends it at the next
+// iteration.  The loop itself is in serve_device.cuh; this file holds the host side
+// and the precompiled kernel (the one specialised to a server's codes is generated
+// at run time by jit.cpp).
 //
 // The automorphisms of a frame are drawn inside the kernel from (seed, frame index):
 // admission launches no kernel, because the persistent kernel holds every SM's shared
