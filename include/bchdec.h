@@ -315,11 +315,14 @@ bch_status bch_server_submit(bch_server *srv, int code_id, const float *llr, int
                              int n_frames, uint64_t autos_seed, uint64_t frame0,
                              uint64_t *request_id);
 /* Collects up to max_ids completed request ids (waiting up to timeout_us for at least
- * one) and admits queued requests that now fit. */
+ * one) and admits queued requests that now fit.  Relaunching a kernel that exited
+ * idle waits at most 30 s for the previous instance; past that BCH_ETIMEOUT, with
+ * the kernel's live-warp and completion counters in bch_last_error(). */
 bch_status bch_server_poll(bch_server *srv, uint64_t *done_ids, int max_ids, int *n_done,
                            int timeout_us);
 /* Copies a completed request's results to caller memory (hard [n][ceil(n/64)], iters,
- * flags; host or device) and releases its memory and slot. */
+ * flags; host or device) and releases its memory and slot.  BCH_ETIMEOUT if the
+ * copies have not finished within 30 s. */
 bch_status bch_server_fetch(bch_server *srv, uint64_t request_id, uint64_t *hard,
                             uint8_t *iters, uint8_t *flags);
 bch_status bch_server_get_stats(bch_server *srv, bch_server_stats *out);
@@ -338,7 +341,10 @@ bch_status bch_server_kernel_info(bch_server *srv, char *buf, size_t capacity);
  * bch_nms_jit_check.  No counterpart in the paper: a build aid. */
 bch_status bch_serve_jit_check(int n_codes, const int *n, const int *k, uint64_t seed, char *log,
                                size_t capacity);
-/* Stops the kernel (at its next chunk boundary) and frees everything. */
+/* Stops the kernel (at its next iteration) and frees everything.  If the kernel or
+ * the server's copies are still running after 30 s, its memory is left allocated
+ * (freeing it under a running kernel would fault) and the reason is kept for
+ * bch_last_error(). */
 void bch_server_destroy(bch_server *srv);
 
 /* Serving benchmark (open loop).  Poisson arrivals at rate_rps for duration_s; each
