@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -68,9 +68,11 @@ def _load():
             "or_build_ho": (i, [i, i, i, u64, i, i, d, d, d, P, P, P]),
             "or_nms_plain": (i, [P, i, i, P, i, i, i, d, i, P, P, P, P, P, P]),
             "or_nms_enhanced": (i, [P, i, i, P, i, i, i, P, i, P, i, P, P, P, P, P, P, P]),
+            "or_nms_plain_f32": (i, [P, i, i, P, i, i, i, C.c_float, i, P, P, P, P]),
+            "or_nms_enhanced_f32": (i, [P, i, i, P, i, i, i, P, i, P, i, P, P, P, P]),
             "or_osd": (i, [P, i, i, P, i, i, i, P, P, P]),
             "or_q16": (d, [d]),
-            "or_nms_enhanced_q": (i, [P, i, i, P, i, i, i, P, i, P, i, i, i, P, P, P, P]),
+            "or_nms_enhanced_q": (i, [P, i, i, P, i, i, i, P, i, P, i, i, i, P, P, P, P, P]),
             "or_ml": (i, [i, i, P, i, i, P]),
             "or_nms_train_grad": (i, [P, i, i, P, i, i, i, P, i, P, P, P, P, P, P, P]),
         }
@@ -268,6 +270,53 @@ def nms_enhanced(Ho, llr, autos, iters, alpha, early_stop=True, trace=False, thr
     return out
 
 
+def nms_plain_f32(H, llr, iters, alpha, early_stop=True, threads=1):
+    """Eqs. (2)-(5) evaluated directly in FP32 (the loops of ``nms_plain``); see the C
+    file: it measures how far a direct single-precision evaluation drifts from FP64."""
+    H = np.ascontiguousarray(H, np.uint8)
+    M, n = H.shape
+    llr = np.ascontiguousarray(llr, np.float32)
+    F, ld = llr.shape
+    hard = np.zeros((F, n), np.uint8)
+    it = np.zeros(F, np.int32)
+    conv = np.zeros(F, np.uint8)
+    y = np.zeros((F, n), np.float64)
+    lib = _load()
+
+    def run(a, b):
+        _check(lib.or_nms_plain_f32(_p(H), M, n, _p(llr[a:]), ld, b - a, iters,
+                                    float(np.float32(alpha)), int(early_stop), _p(hard[a:]),
+                                    _p(it[a:]), _p(conv[a:]), _p(y[a:])), "nms_plain_f32")
+
+    _pool_map(run, F, 256, threads)
+    return dict(hard=hard, iters=it, converged=conv, y=y)
+
+
+def nms_enhanced_f32(Ho, llr, autos, iters, alpha, early_stop=True, threads=1):
+    """Algorithm 1 (reading A) evaluated directly in FP32 (the loops of
+    ``nms_enhanced``); see the C file."""
+    Ho = np.ascontiguousarray(Ho, np.uint8)
+    M, n = Ho.shape
+    llr = np.ascontiguousarray(llr, np.float32)
+    F, ld = llr.shape
+    autos = np.ascontiguousarray(autos, np.uint16).reshape(F, -1)
+    P = autos.shape[1]
+    al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float32), (iters,)))
+    hard = np.zeros((F, n), np.uint8)
+    it = np.zeros(F, np.int32)
+    conv = np.zeros(F, np.uint8)
+    y = np.zeros((F, n), np.float64)
+    lib = _load()
+
+    def run(a, b):
+        _check(lib.or_nms_enhanced_f32(_p(Ho), M, n, _p(llr[a:]), ld, b - a, P, _p(autos[a:]),
+                                       iters, _p(al), int(early_stop), _p(hard[a:]), _p(it[a:]),
+                                       _p(conv[a:]), _p(y[a:])), "nms_enhanced_f32")
+
+    _pool_map(run, F, 256, threads)
+    return dict(hard=hard, iters=it, converged=conv, y=y)
+
+
 def q16(x: float) -> float:
     return _load().or_q16(float(x))
 
@@ -285,15 +334,19 @@ def nms_enhanced_q(Ho, llr, autos, iters, alpha, fmt, rescale=False, early_stop=
     it = np.zeros(F, np.int32)
     conv = np.zeros(F, np.uint8)
     y = np.zeros((F, n), np.float64)
+    margin = np.zeros(F, np.float64)
     lib = _load()
 
     def run(a, b):
         _check(lib.or_nms_enhanced_q(_p(Ho), M, n, _p(llr[a:]), ld, b - a, P, _p(autos[a:]), iters,
                                      _p(al), int(early_stop), fmt, int(rescale), _p(hard[a:]),
-                                     _p(it[a:]), _p(conv[a:]), _p(y[a:])), "nms_enhanced_q")
+                                     _p(it[a:]), _p(conv[a:]), _p(y[a:]), _p(margin[a:])),
+               "nms_enhanced_q")
 
     _pool_map(run, F, 256, threads)
-    return dict(hard=hard, iters=it, converged=conv, y=y)
+    # margin (FP16 only): smallest distance of a merged value, relative to its operand
+    # magnitude, to zero or to a binary16 rounding boundary (see the C file)
+    return dict(hard=hard, iters=it, converged=conv, y=y, margin=margin)
 
 
 def osd(H, llr, order=2, threads=1, return_mrb=False):

@@ -33,6 +33,10 @@
  *                                     generator-side basis.
  *   or_ml                             pinned: corrects every <= t error pattern.
  *   or_nms_train_grad                 pinned: central finite differences.
+ *   or_nms_plain_f32,                 pinned: hand-derived examples reproduced exactly,
+ *   or_nms_enhanced_f32               one iteration within the textbook rounding-error
+ *                                     bound of a float sum, decisions equal to the
+ *                                     FP64 decoder's on unambiguous frames.
  *   or_nms_enhanced_q, or_q16         pinned: binary16 rounding against numpy's
  *                                     float16; quantised decode equals the FP64 decode
  *                                     on inputs that are exact in the format.
@@ -992,6 +996,142 @@ int or_nms_enhanced(const uint8_t *Ho, int M, int n, const float *llr, int ld, i
   return OR_OK;
 }
 
+
+/* ------------------------------------------------------------------------------
+ * Single-precision restatements of the two decoders (Eqs. (2)-(5) and Algorithm 1,
+ * reading A): the same loops, in the same order, as or_nms_plain and
+ * or_nms_enhanced, with every value held in float (IEEE binary32, each operation
+ * rounded once; the build turns off contraction into fused multiply-adds).  They
+ * model no kernel: their only use is to measure how far a direct FP32 evaluation of
+ * the method drifts from the FP64 result over many iterations, the evidence behind
+ * the trajectory tolerance of the parity tests.  Outputs as in the FP64 versions
+ * (y_out widened to double).
+ * ---------------------------------------------------------------------------- */
+static float c2v_literal_f32(const float *v2c_row, int w, int self, float alpha) {
+  float sg = 1.0f, mn = INFINITY;
+  for (int e = 0; e < w; e++) {
+    if (e == self) continue;
+    float x = v2c_row[e];
+    if (x < 0.0f) sg = -sg;
+    float a = fabsf(x);
+    if (a < mn) mn = a;
+  }
+  return alpha * sg * mn;
+}
+
+int or_nms_plain_f32(const uint8_t *H, int M, int n, const float *llr, int ld, int F, int iters,
+                     float alpha, int early_stop, uint8_t *hard, int *iters_used,
+                     uint8_t *converged, double *y_out) {
+  float *c2v = (float *)calloc((size_t)M * n, sizeof(float));
+  float *nc2v = (float *)calloc((size_t)M * n, sizeof(float));
+  float *v2c = (float *)calloc((size_t)M * n, sizeof(float));
+  int *vars = (int *)malloc(sizeof(int) * (size_t)n);
+  float x[128], rowbuf[128];
+  uint8_t c[128];
+  if (!c2v || !nc2v || !v2c || !vars) { free(c2v); free(nc2v); free(v2c); free(vars); return OR_ENOMEM; }
+  for (int f = 0; f < F; f++) {
+    const float *L = llr + (size_t)f * ld;
+    memset(c2v, 0, sizeof(float) * (size_t)M * n);
+    int t_run = 0, ok = 0;
+    for (int i = 0; i < n; i++) {
+      x[i] = L[i];
+      c[i] = x[i] < 0.0f;
+    }
+    for (int t = 1; t <= iters; t++) {
+      for (int j = 0; j < M; j++) /* Eq. (2) */
+        for (int i = 0; i < n; i++) {
+          if (!H[j * n + i]) continue;
+          float s = L[i];
+          for (int kk = 0; kk < M; kk++)
+            if (kk != j && H[kk * n + i]) s += c2v[kk * n + i];
+          v2c[j * n + i] = s;
+        }
+      for (int j = 0; j < M; j++) { /* Eq. (3) */
+        int w = row_vars(H, n, j, vars);
+        for (int e = 0; e < w; e++) rowbuf[e] = v2c[j * n + vars[e]];
+        for (int e = 0; e < w; e++) nc2v[j * n + vars[e]] = c2v_literal_f32(rowbuf, w, e, alpha);
+      }
+      memcpy(c2v, nc2v, sizeof(float) * (size_t)M * n);
+      for (int i = 0; i < n; i++) { /* Eq. (4) */
+        float s = L[i];
+        for (int j = 0; j < M; j++)
+          if (H[j * n + i]) s += c2v[j * n + i];
+        x[i] = s;
+        c[i] = s < 0.0f;
+      }
+      t_run = t;
+      ok = or_syndrome_weight(H, M, n, c) == 0;
+      if (early_stop && ok) break;
+    }
+    if (hard) memcpy(hard + (size_t)f * n, c, (size_t)n);
+    if (iters_used) iters_used[f] = t_run;
+    if (converged) converged[f] = (uint8_t)ok;
+    if (y_out)
+      for (int i = 0; i < n; i++) y_out[(size_t)f * n + i] = (double)x[i];
+  }
+  free(c2v); free(nc2v); free(v2c); free(vars);
+  return OR_OK;
+}
+
+int or_nms_enhanced_f32(const uint8_t *Ho, int M, int n, const float *llr, int ld, int F, int P,
+                        const uint16_t *autos, int iters, const float *alpha, int early_stop,
+                        uint8_t *hard, int *iters_used, uint8_t *converged, double *y_out) {
+  float y[128], yn[128], z[128], S[128], sum[128], rowbuf[128];
+  int vars[128], pi[128];
+  uint8_t c[128];
+  for (int f = 0; f < F; f++) {
+    const float *L = llr + (size_t)f * ld;
+    const uint16_t *aut = autos + (size_t)f * P;
+    int escale = 0; /* y is kept in units of 2^escale (see below) */
+    for (int i = 0; i < n; i++) {
+      y[i] = L[i];
+      c[i] = y[i] < 0.0f;
+    }
+    int t_run = 0, ok = 0;
+    for (int t = 1; t <= iters; t++) {
+      for (int i = 0; i < n; i++) sum[i] = 0.0f;
+      for (int p = 0; p < P; p++) {
+        for (int i = 0; i < n; i++) {
+          pi[i] = auto_apply(aut[p], n, i);
+          z[pi[i]] = y[i];
+        }
+        for (int u = 0; u < n; u++) S[u] = 0.0f;
+        for (int j = 0; j < M; j++) {
+          int w = row_vars(Ho, n, j, vars);
+          for (int e = 0; e < w; e++) rowbuf[e] = z[vars[e]];
+          for (int e = 0; e < w; e++) S[vars[e]] += c2v_literal_f32(rowbuf, w, e, alpha[t - 1]);
+        }
+        for (int i = 0; i < n; i++) sum[i] += S[pi[i]];
+      }
+      float mx = 0.0f;
+      for (int i = 0; i < n; i++) {
+        yn[i] = y[i] + sum[i] / (float)P;
+        c[i] = yn[i] < 0.0f;
+        if (fabsf(yn[i]) > mx) mx = fabsf(yn[i]);
+      }
+      memcpy(y, yn, sizeof(float) * (size_t)n);
+      /* y grows about tenfold per iteration and leaves the FP32 range within 32
+       * iterations on the n = 127 codes; an FP32 evaluation therefore has to keep y
+       * in range.  Scaling by a power of two is exact and Algorithm 1 is homogeneous
+       * of degree one in y (min-sum is scale invariant), so past 2^100 the frame is
+       * divided by 2^64 and the exponent remembered. */
+      if (mx > 0x1p100f) {
+        for (int i = 0; i < n; i++) y[i] *= 0x1p-64f;
+        escale += 64;
+      }
+      t_run = t;
+      ok = or_syndrome_weight(Ho, M, n, c) == 0;
+      if (early_stop && ok) break;
+    }
+    if (hard) memcpy(hard + (size_t)f * n, c, (size_t)n);
+    if (iters_used) iters_used[f] = t_run;
+    if (converged) converged[f] = (uint8_t)ok;
+    if (y_out)
+      for (int i = 0; i < n; i++) y_out[(size_t)f * n + i] = ldexp((double)y[i], escale);
+  }
+  return OR_OK;
+}
+
 /* ------------------------------------------------------------------------------
  * Reduced-precision storage of the enhanced decoder (the library's FP16 and 8-bit
  * message formats), restated with the quantisers applied at the same points:
@@ -1024,12 +1164,45 @@ static double q8(double x) {
   return r;
 }
 
+/* Distance from x to the nearest input at which binary16 rounding (as or_q16) changes
+ * its result: the midpoints (j + 1/2) q between neighbouring binary16 values of
+ * spacing q, and 65488 below the saturation value. */
+/* Distance from x to the nearest input at which binary16 rounding (as or_q16) changes
+ * its result: the midpoints (j + 1/2) q between neighbouring binary16 values of
+ * spacing q, and 65488 below the saturation value. */
+static double q16_boundary_dist(double x) {
+  double a = fabs(x);
+  if (a >= 65504.0) return a - 65488.0;
+  if (a == 0.0) return ldexp(1.0, -25);
+  int E;
+  frexp(a, &E);
+  double q = (E - 1 < -14) ? ldexp(1.0, -24) : ldexp(1.0, E - 1 - 10);
+  double fr = a / q - floor(a / q);
+  return fabs(fr - 0.5) * q;
+}
+
+/* Largest power of two dividing a nonzero binary16 value x: x = M q with q the
+ * spacing of its binade and M an integer below 2^11; the lowest set bit of M. */
+static double q16_spacing(double x) {
+  double a = fabs(x);
+  int E;
+  frexp(a, &E); /* a = f 2^E, f in [0.5, 1) */
+  double q = (E - 1 < -14) ? ldexp(1.0, -24) : ldexp(1.0, E - 1 - 10);
+  long long M = (long long)(a / q);
+  while ((M & 1) == 0) {
+    M >>= 1;
+    q *= 2.0;
+  }
+  return q;
+}
+
 int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld, int F, int P,
                       const uint16_t *autos, int iters, const double *alpha, int early_stop,
                       int fmt, int rescale, uint8_t *hard, int *iters_used, uint8_t *converged,
-                      double *y_out) {
+                      double *y_out, double *margin) {
   if (fmt != 1 && fmt != 2) return OR_EARG;
-  double y[128], yn[128], z[128], S[128], sum[128], rowbuf[128];
+  double y[128], yn[128], z[128], S[128], Sa[128], sum[128], suma[128], rowbuf[128];
+  double Sq[128], qmin[128];
   int vars[128], pi[128];
   uint8_t c[128];
   const double lim = fmt == 1 ? 16384.0 : 31.0;
@@ -1037,6 +1210,7 @@ int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld,
     const float *L = llr + (size_t)f * ld;
     const uint16_t *aut = autos + (size_t)f * P;
     int escale = 0;
+    double mar = INFINITY;
     for (int i = 0; i < n; i++) {
       double x = (double)L[i];
       y[i] = fmt == 1 ? or_q16(x) : q8(4.0 * x);
@@ -1044,16 +1218,21 @@ int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld,
     }
     int t_run = 0, ok = 0;
     for (int t = 1; t <= iters; t++) {
-      for (int i = 0; i < n; i++) sum[i] = 0.0;
+      for (int i = 0; i < n; i++) { sum[i] = 0.0; suma[i] = 0.0; qmin[i] = INFINITY; }
       for (int p = 0; p < P; p++) {
         for (int i = 0; i < n; i++) {
           pi[i] = auto_apply(aut[p], n, i);
           z[pi[i]] = y[i];
         }
-        for (int u = 0; u < n; u++) S[u] = 0.0;
+        for (int u = 0; u < n; u++) { S[u] = 0.0; Sa[u] = 0.0; Sq[u] = INFINITY; }
         for (int j = 0; j < M; j++) {
           int w = row_vars(Ho, n, j, vars);
-          for (int e = 0; e < w; e++) rowbuf[e] = z[vars[e]];
+          double m1 = INFINITY;
+          for (int e = 0; e < w; e++) {
+            rowbuf[e] = z[vars[e]];
+            if (fabs(rowbuf[e]) < m1) m1 = fabs(rowbuf[e]);
+          }
+          double v1 = or_q16(alpha[t - 1] * m1); /* the row's smallest c2v magnitude */
           for (int e = 0; e < w; e++) {
             double sg = 1.0, mn = INFINITY;
             for (int e2 = 0; e2 < w; e2++) {
@@ -1064,9 +1243,16 @@ int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld,
             double mag = alpha[t - 1] * mn;
             mag = fmt == 1 ? or_q16(mag) : rint(mag);
             S[vars[e]] += sg * mag;
+            Sa[vars[e]] += mag + v1;
+            if (mag != 0.0 && q16_spacing(mag) < Sq[vars[e]]) Sq[vars[e]] = q16_spacing(mag);
+            if (v1 != 0.0 && q16_spacing(v1) < Sq[vars[e]]) Sq[vars[e]] = q16_spacing(v1);
           }
         }
-        for (int i = 0; i < n; i++) sum[i] += S[pi[i]];
+        for (int i = 0; i < n; i++) {
+          sum[i] += S[pi[i]];
+          suma[i] += Sa[pi[i]];
+          if (Sq[pi[i]] < qmin[i]) qmin[i] = Sq[pi[i]];
+        }
       }
       double mx = 0.0;
       for (int i = 0; i < n; i++) {
@@ -1083,6 +1269,28 @@ int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld,
         }
         escale += k;
       }
+      /* margin (FP16).  Every term of the merged numerator P y_i + sum of c2v, and
+       * the row minimum alpha m1 of every row of the variable, is a multiple of qm
+       * (the smallest binary16 spacing among them).  If their magnitudes add up to
+       * tot < 2^24 qm, every partial sum of those terms, in any order, is an integer
+       * multiple of qm below 2^24 qm and therefore exact in FP32: a decoder that
+       * accumulates in FP32 and rounds the exact quotient gets the same binary16
+       * value.  Otherwise its FP32 sum errs by a small multiple of 2^-24 tot, and the
+       * stored value can only differ if the exact merged value lies that close to
+       * zero (its sign is the hard decision) or to a point where its binary16
+       * rounding changes.  mar is the smallest such distance relative to tot / P over
+       * the non-exact merges of the decode (infinite when every merge is exact). */
+      if (fmt == 1)
+        for (int i = 0; i < n; i++) {
+          double tot = (double)P * fabs(y[i]) + suma[i];
+          double qm = qmin[i];
+          if (y[i] != 0.0 && q16_spacing(y[i]) < qm) qm = q16_spacing(y[i]);
+          if (tot <= 0.0 || tot < ldexp(qm, 24)) continue;
+          double d = fabs(yn[i]);
+          double b = q16_boundary_dist(yn[i] * sc) / sc;
+          if (b < d) d = b;
+          if (d / (tot / (double)P) < mar) mar = d / (tot / (double)P);
+        }
       for (int i = 0; i < n; i++) y[i] = fmt == 1 ? or_q16(yn[i] * sc) : q8(yn[i] * sc);
       t_run = t;
       ok = or_syndrome_weight(Ho, M, n, c) == 0;
@@ -1094,6 +1302,7 @@ int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld,
     if (y_out)
       for (int i = 0; i < n; i++)
         y_out[(size_t)f * n + i] = ldexp(fmt == 1 ? y[i] : y[i] / 4.0, escale);
+    if (margin) margin[f] = mar;
   }
   return OR_OK;
 }
