@@ -218,17 +218,20 @@ bch_status bch_hybrid_decode(const bch_code *code, const bch_code *std_code,
 
 /* bch_hybrid_decode for callers that cannot allocate device memory when they decode
  * (real-time loops where cudaMalloc is forbidden or too slow after start-up, plug-ins
- * handed only pre-registered buffers): the same arguments minus the workspace.  The
- * paper has no counterpart; this is a deployment convenience.  Its scratch is one
- * file-scope __device__ array of about 1 MB that every GPU loading the library holds
- * until exit, so n_frames is limited to 262144 (larger batches return BCH_EINVAL).
- * The first call on a device looks the array up (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Calls share the
- * array: calls that overlap on the GPU (different streams or devices' contexts at the
- * same time) race and must be serialised by the caller; each call clears what must
- * start at zero.  No cudaMalloc, cudaFree or allocating routine is called and only
- * precompiled kernels run; results equal bch_hybrid_decode's within the FP32
- * tolerance (bit-exact for integer work). */
+ * handed only pre-registered buffers): the same arguments minus the workspace, checked
+ * by the same rules (n_autos = 0 selects the plain decoder) before anything is
+ * launched, so a rejected call writes nothing.  The paper has no counterpart; this is
+ * a deployment convenience.  Its scratch is one file-scope __device__ array of about
+ * 1 MB that every GPU loading the library holds until exit, so n_frames is limited to
+ * 262144 (larger batches return BCH_EINVAL).  The first call in a CUDA context looks
+ * the array up (cudaGetSymbolAddress) with that context current -- again after the
+ * context is re-created, e.g. by cudaDeviceReset; make that first call before any
+ * stream capture.  Each device has its own array, shared by every call on that device:
+ * calls that overlap on the same GPU (different streams at the same time) race and
+ * must be serialised by the caller; each call clears what must start at zero.  No
+ * cudaMalloc, cudaFree or allocating routine is called and only precompiled kernels
+ * run; results equal bch_hybrid_decode's within the FP32 tolerance (bit-exact for
+ * integer work). */
 bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_code *std_code,
                                      const bch_nms_params *params, const float *llr, int ld,
                                      int n_frames, const uint16_t *autos, uint64_t *hard,

@@ -93,4 +93,10 @@ struct bch_code {
 namespace bchlib {
 void set_error(const std::string &msg);
 bch_status fail(bch_status s, const std::string &msg);
+// Argument checks shared by the decode entry points (BCH_EINVAL with a message).
+bch_status check_params(const bch_code *code, const bch_nms_params *p);
+bch_status check_frames(const bch_code *code, const float *llr, int ld, int F);
+// The OSD stage's requirements: std_code is the standard matrix of the same code as
+// `code` (when given), n - k <= 64, order in 0..2.
+bch_status check_osd(const bch_code *code, const bch_code *std_code, int order);
 }  // namespace bchlib

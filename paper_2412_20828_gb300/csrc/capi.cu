@@ -144,6 +144,10 @@ WsLayout ws_layout(int F, int iters) {
 
 bool code_ok(const bch_code *c) { return c != nullptr && c->dev_dc != nullptr; }
 
+}  // namespace
+
+namespace bchlib {
+
 bch_status check_params(const bch_code *code, const bch_nms_params *p) {
   if (!code_ok(code)) return fail(BCH_EINVAL, "null code");
   if (!p) return fail(BCH_EINVAL, "null params");
@@ -164,6 +168,20 @@ bch_status check_frames(const bch_code *code, const float *llr, int ld, int F) {
   if (F > 0 && !llr) return fail(BCH_EINVAL, "llr is null");
   return BCH_OK;
 }
+
+bch_status check_osd(const bch_code *code, const bch_code *std_code, int order) {
+  if (!code_ok(std_code) || std_code->kind != BCH_PCM_STANDARD)
+    return fail(BCH_EINVAL, "OSD needs the standard parity-check matrix");
+  if (code && (!code_ok(code) || std_code->alg.n != code->alg.n || std_code->alg.k != code->alg.k))
+    return fail(BCH_EINVAL, "std_code must be the standard matrix of the same code");
+  if (order < 0 || order > 2) return fail(BCH_EINVAL, "OSD order must be 0, 1 or 2");
+  if (std_code->alg.n - std_code->alg.k > 64) return fail(BCH_EINVAL, "OSD supports n-k <= 64");
+  return BCH_OK;
+}
+
+}  // namespace bchlib
+
+namespace {
 
 // Builds the device image of a code: rows grouped by weight, column codes, row masks,
 // parity words.
@@ -560,11 +578,9 @@ bch_status bch_nms_decode(const bch_code *code, const bch_nms_params *params, co
 static bch_status run_osd(const bch_code *std_code, int order, const float *llr, int ld,
                           const uint32_t *list, const uint32_t *count, int max_frames, uint64_t *hard,
                           uint8_t *flags, unsigned *queue, cudaStream_t st) {
-  if (!code_ok(std_code) || std_code->kind != BCH_PCM_STANDARD)
-    return fail(BCH_EINVAL, "OSD needs the standard parity-check matrix");
-  if (order < 0 || order > 2) return fail(BCH_EINVAL, "OSD order must be 0, 1 or 2");
+  bch_status s = check_osd(nullptr, std_code, order);
+  if (s != BCH_OK) return s;
   const int n = std_code->alg.n, M = n - std_code->alg.k;
-  if (M > 64) return fail(BCH_EINVAL, "OSD supports n-k <= 64");
   if (max_frames <= 0) return BCH_OK;
   OsdArgs a;
   a.n = n;
@@ -604,10 +620,11 @@ bch_status bch_hybrid_decode(const bch_code *code, const bch_code *std_code, con
                              uint32_t *failed_count, void *workspace, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!hard || !flags) return fail(BCH_EINVAL, "hybrid decoding needs hard and flags");
-  if (!code_ok(std_code) || std_code->alg.n != (code_ok(code) ? code->alg.n : -1) ||
-      std_code->alg.k != code->alg.k)
-    return fail(BCH_EINVAL, "std_code must be the standard matrix of the same code");
-  bch_status s = run_nms(code, params, llr, ld, n_frames, autos, hard, iters, flags, llr_out, nullptr,
+  // every argument is checked before the first launch, so a rejected call writes nothing
+  bch_status s = check_params(code, params);
+  if (s == BCH_OK) s = check_osd(code, std_code, params->osd_order);
+  if (s != BCH_OK) return s;
+  s = run_nms(code, params, llr, ld, n_frames, autos, hard, iters, flags, llr_out, nullptr,
                          workspace, st);
   if (s != BCH_OK || n_frames == 0) return s;
   const WsLayout L = ws_layout(n_frames, params->iters);

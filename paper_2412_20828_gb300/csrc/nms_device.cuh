@@ -73,15 +73,40 @@ __device__ __forceinline__ float ld_y(const float *p) { return *p; }
 __device__ __forceinline__ float ld_y(const __half *p) { return __half2float(*p); }
 __device__ __forceinline__ int ld_y(const int8_t *p) { return int(*p); }
 
+// A binary16 zero is stored as +0, so that the sign-bit tests of the decoder read it
+// as non-negative (sgn(0) = +1), also when a tiny negative value rounded to zero.
+__device__ __forceinline__ __half half_pz(__half h) {
+  return __half2float(h) == 0.0f ? __float2half_rn(0.0f) : h;
+}
 // FP16 store: round to nearest even, saturating at +-65504.
 __device__ __forceinline__ __half to_half_sat(float x) {
   x = fminf(fmaxf(x, -65504.0f), 65504.0f);
-  return __float2half_rn(x);
+  return half_pz(__float2half_rn(x));
 }
 __device__ __forceinline__ __half half_sat_d(double x) {
   x = fmin(fmax(x, -65504.0), 65504.0);
   return __double2half(x);
 }
+// FP16 merge: the binary16 value nearest to num / P (num = P y + sum of c2v), ties
+// to even, saturating at +-65504, with num exact.  The FP32 quotient q = fl(num / P)
+// lies on the same side of every binary16 rounding point as the exact quotient (RN is
+// monotone and those points are FP32 values), so rounding q gives the right result
+// unless q landed exactly on a midpoint the exact quotient is not on; then the sign
+// of num - mid P (an exact product, one rounding that keeps the sign) picks the side.
+__device__ __forceinline__ __half half_of_quotient(float num, float P) {
+  const float q = __fdiv_rn(num, P);
+  if (fabsf(q) >= 65504.0f) return __float2half_rn(copysignf(65504.0f, q));
+  const __half lo = __float2half_rd(q), hi = __float2half_ru(q);
+  const float mid = 0.5f * (__half2float(lo) + __half2float(hi));
+  __half h = __float2half_rn(q);
+  if (q == mid && __half2float(lo) != __half2float(hi)) {
+    const float d = __fmaf_rn(-mid, P, num);
+    if (d > 0.0f) h = hi;
+    if (d < 0.0f) h = lo;
+  }
+  return half_pz(h);
+}
+
 // INT8 store: rne, saturating at +-31 (LSB = 1/4 of an LLR unit).
 __device__ __forceinline__ int8_t to_q(float x) {
   int q = __float2int_rn(x);
@@ -409,25 +434,30 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         escale += 64;
       }
     } else {
-      // pass 1: FP32 merge into the accumulator slot, track the magnitude
+      // pass 1: the merged value into the accumulator slot, track the magnitude.
+      // INT8: q + (integer sum) / P with a correctly rounded division (a .5 tie stays
+      // a tie).  FP16: the numerator num = P y + sum of c2v, exact whenever the FP32
+      // accumulation of binary16 values was; y_new = num / P is rounded once, below.
+      const float fP = float(a.P);
       float mx = 0.0f;
 #pragma unroll
       for (int i = 0; i < NW * 32; i++) {
         if (i < n) {
           float yn;
-          if constexpr (MSG == kINT8)  // exact division: a .5 tie stays a tie
-            yn = float(ld_y(y + (i * kShift))) + __fdiv_rn(float(acc[i * kShift]), float(a.P));
+          if constexpr (MSG == kINT8)
+            yn = float(ld_y(y + (i * kShift))) + __fdiv_rn(float(acc[i * kShift]), fP);
           else
-            yn = __fmaf_rn(acc[i * kShift], invP, ld_y(y + (i * kShift)));
+            yn = __fmaf_rn(ld_y(y + (i * kShift)), fP, acc[i * kShift]);
           cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
           mx = fmaxf(mx, fabsf(yn));
           reinterpret_cast<float *>(acc)[i * kShift] = yn;
         }
       }
-      // optional power-of-two renormalisation (exact; min-sum is scale invariant)
+      // optional power-of-two renormalisation (exact; min-sum is scale invariant):
+      // halve while max |y_new| > lim (FP16: compared on the numerators, exactly)
       float sc = 1.0f;
       if (a.rescale) {
-        const float lim = (MSG == kINT8) ? 31.0f : 16384.0f;
+        const float lim = (MSG == kINT8) ? 31.0f : 16384.0f * fP;
         int k = 0;
         while (mx * sc > lim && k < 126) {
           sc *= 0.5f;
@@ -442,7 +472,7 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
           if constexpr (MSG == kINT8)
             y[i * kShift] = to_q(yn);
           else
-            y[i * kShift] = to_half_sat(yn);
+            y[i * kShift] = half_of_quotient(yn, fP);
           acc[i * kShift] = A(0);
         }
       }

@@ -25,26 +25,61 @@ constexpr size_t kScratchBytes = kCountOff + 256;
 
 // Every GPU that loads the library holds this array until the process exits.  In host
 // code its name is only a host-side stand-in; the device address comes from
-// cudaGetSymbolAddress, looked up once per device.
+// cudaGetSymbolAddress, looked up once per device and context (below).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// The address is looked up once per device and context: a context created anew on the
+// same device (after cudaDeviceReset, for instance) has its own copy of the array, so
+// the cache is keyed by the driver's unique context id (cuCtxGetId, reached through
+// cudaGetDriverEntryPointByVersion so that the library does not link libcuda).
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
+
+using CtxGetCurrentFn = int (*)(void **);
+using CtxGetIdFn = int (*)(void *, unsigned long long *);
+
+bool current_context_id(unsigned long long *id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(fn);
+  });
+  void *ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
 
 bch_status scratch_address(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(BCH_EINVAL, "device ordinal out of range");
+  // initialises the device's primary context (a no-op once it exists) and makes it
+  // current, so that its id can be read
+  e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("device set-up: ") + cudaGetErrorString(e));
+  unsigned long long id = 0;
+  if (!current_context_id(&id)) return fail(BCH_ECUDA, "cannot identify the current CUDA context");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev] || g_ctx_id[dev] != id) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return fail(BCH_ECUDA, std::string("cudaGetSymbolAddress of the no-allocation scratch: ") +
                                  cudaGetErrorString(e));
     g_addr[dev] = p;
+    g_ctx_id[dev] = id;
   }
   *out = g_addr[dev];
   return BCH_OK;
@@ -57,20 +92,19 @@ extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_
                                                 int n_frames, const uint16_t *autos, uint64_t *hard,
                                                 uint8_t *iters, uint8_t *flags, float *llr_out,
                                                 void *stream) {
-  if (!code || !code->dev_dc || !std_code || !std_code->dev_dc) return fail(BCH_EINVAL, "null code");
-  if (std_code->kind != BCH_PCM_STANDARD || std_code->alg.n != code->alg.n || std_code->alg.k != code->alg.k)
-    return fail(BCH_EINVAL, "std_code must be the standard matrix of the same code");
-  if (!p || !p->alpha || p->iters < 1 || p->iters > 32 || p->n_autos < 1 || p->n_autos > 9 ||
-      p->msg < BCH_MSG_FP32 || p->msg > BCH_MSG_INT8 || p->osd_order < 0 || p->osd_order > 2)
-    return fail(BCH_EINVAL, "bad decoder parameters");
-  if (n_frames < 0 || ld < code->alg.n) return fail(BCH_EINVAL, "bad frame layout");
+  // the same argument checks as bch_hybrid_decode, all before the first launch
+  bch_status s = check_params(code, p);
+  if (s == BCH_OK) s = check_osd(code, std_code, p->osd_order);
+  if (s == BCH_OK) s = check_frames(code, llr, ld, n_frames);
+  if (s != BCH_OK) return s;
   if (n_frames > kNoallocMaxFrames)
     return fail(BCH_EINVAL, "n_frames exceeds the 262144 frames the no-allocation scratch holds; "
                             "split the batch or use bch_hybrid_decode with a workspace");
   if (n_frames == 0) return BCH_OK;
-  if (!llr || !autos || !hard || !flags) return fail(BCH_EINVAL, "null buffer");
+  if (!hard || !flags) return fail(BCH_EINVAL, "hybrid decoding needs hard and flags");
+  if (p->n_autos > 0 && !autos) return fail(BCH_EINVAL, "autos is null");
   void *base = nullptr;
-  bch_status s = scratch_address(&base);
+  s = scratch_address(&base);
   if (s != BCH_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned char *ws = static_cast<unsigned char *>(base);
@@ -107,7 +141,6 @@ extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_
   if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("compaction: ") + cudaGetErrorString(e));
 
   const int n = std_code->alg.n, M = n - std_code->alg.k;
-  if (M > 64) return fail(BCH_EINVAL, "OSD supports n-k <= 64");
   OsdArgs o;
   o.n = n;
   o.k = std_code->alg.k;

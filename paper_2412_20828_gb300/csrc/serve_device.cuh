@@ -281,16 +281,20 @@ __device__ __forceinline__ void serve_loop(const SrvArgs &a, unsigned char *smem
     }
     // ---- count finished frames: per request, one of the lanes that finished frames
     // of it adds them all to the request's done counter, and the add that completes
-    // the request posts it
+    // the request posts it.  The warp barrier orders every lane's result writes (the
+    // OSD's, made by whichever lanes ran it, included) before the counting lane's
+    // fence, and that fence is cumulative: it orders everything the counting lane has
+    // observed before its add, so a warp that later completes the request (and fences
+    // before posting it) publishes results that are all in memory.
     const unsigned dmask = __ballot_sync(kFull, done);
     if (dmask) {
-      if (done) __threadfence();  // this lane's result writes
-      __syncwarp();               // ... and every other lane's (the OSD's included)
+      __syncwarp();
       if (done) {
         const unsigned peers = __match_any_sync(dmask, slot);
         if (lane == __ffs(peers) - 1) {
           const SrvSlot sl = load_slot(a.slots + slot);
           const unsigned cnt = unsigned(__popc(peers));
+          __threadfence();
           const unsigned d = atomicAdd(&a.slots[slot].done, cnt) + cnt;
           if (int(d) == sl.F) {
             const unsigned ci = atomicAdd(&a.dv->comp_tail, 1u);

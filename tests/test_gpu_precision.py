@@ -3,9 +3,16 @@
 INT8 (with and without power-of-two renormalisation): every quantiser input is an
 exact integer combination or a correctly-rounded division whose .5 ties are exact, so
 hard decisions, iteration counts and final values are bit-exact on every frame.
-FP16: the FP32 accumulation of binary16 messages decides rare binary16 roundings
-differently from the oracle's exact sums; the first iteration is compared within one
-binary16 ulp and full decodes must agree on >= 99% of frames.
+FP16: the binary16 check-to-variable values are formed exactly and rounded once on
+both sides, so the only difference is that the kernel accumulates them in FP32 where
+the oracle's sums are exact.  Its FP32 sum of K terms errs by at most (K + 2) 2^-24
+of the operand magnitude (K <= 3 x column weight + 4, below 5e-6 for every code here),
+so a stored binary16 value can differ only where the exact merged value lies within
+that distance of a binary16 rounding boundary or of zero.  The oracle reports, per
+frame, the smallest such distance over the whole decode (``margin``); frames whose
+margin is below FP16_AMBIG = 2e-5 (4x the error bound) or whose channel LLR has some
+|L| < 1e-3 are ambiguous, and every other frame must be bit-exact: hard decisions,
+iteration counts, flags and final values.
 """
 import numpy as np
 import pytest
@@ -17,6 +24,7 @@ from paper_2412_20828_gb300 import bchdec as B
 pytestmark = pytest.mark.gpu
 
 ALPHA = float(np.float32(0.78))
+FP16_AMBIG = 2e-5
 
 
 @pytest.fixture(scope="module")
@@ -58,13 +66,13 @@ def test_int8_bit_exact(torch_cuda, nk, rescale):
     assert np.array_equal(g["y"].astype(np.float64), ref["y"])
 
 
-@pytest.mark.parametrize("nk", [(63, 45), (127, 64)])
+@pytest.mark.parametrize("nk,ebn0", [((63, 45), 2.5), ((127, 64), 3.5), ((127, 99), 3.5)])
 @pytest.mark.parametrize("rescale", [False, True])
-def test_fp16_close_to_oracle(torch_cuda, nk, rescale):
+def test_fp16_close_to_oracle(torch_cuda, nk, ebn0, rescale):
     n, k = nk
     c = B.Code(n, k)
     F = 800
-    cw, llr = frames(n, k, F, 2.5, 950 + n + k, ld=(n + 3) & ~3)
+    cw, llr = frames(n, k, F, ebn0, 950 + n + k, ld=(n + 3) & ~3)
     autos = O.draw_autos(n, 3, 37, 0, F)
     # first iteration: within one binary16 ulp of the oracle
     g1 = decode(torch_cuda, c, llr, autos, 1, B.MSG_FP16, rescale, early_stop=False)
@@ -74,8 +82,19 @@ def test_fp16_close_to_oracle(torch_cuda, nk, rescale):
     assert np.all(np.abs(g1["y"] - r1["y"]) <= np.maximum(ulp, 2 ** -24) * 1.0001)
     g = decode(torch_cuda, c, llr, autos, 12, B.MSG_FP16, rescale)
     ref = O.nms_enhanced_q(c.dense(), llr, autos, 12, ALPHA, 1, rescale=rescale, threads=None)
-    agree = np.all(g["hard"] == ref["hard"], axis=1) & (g["iters"] == ref["iters"])
-    assert agree.mean() >= 0.99
+    amb = (ref["margin"] < FP16_AMBIG) | np.any(np.abs(llr[:, :n]) < 1e-3, axis=1)
+    # long decodes of BCH(127,64) meet many non-exact merges (saturated or renormalised
+    # frames next to tiny values), about a quarter of its frames
+    assert amb.mean() < 0.3
+    # over all frames (the ambiguous ones included) the frame error counts agree
+    e_g = int(np.any(g["hard"] != cw, axis=1).sum())
+    e_r = int(np.any(ref["hard"] != cw, axis=1).sum())
+    assert abs(e_g - e_r) <= 3 * np.sqrt(e_g + e_r + 1)
+    ok = ~amb
+    assert np.array_equal(g["hard"][ok], ref["hard"][ok])
+    assert np.array_equal(g["iters"][ok], ref["iters"][ok])
+    assert np.array_equal(g["flags"][ok] & 1, ref["converged"][ok])
+    assert np.array_equal(g["y"][ok].astype(np.float64), ref["y"][ok])
 
 
 def test_fer_sweep_small(torch_cuda):

@@ -1,12 +1,13 @@
 """Continuous-batching server: results are the same alone and in a mixed stream, equal
-to the batch hybrid decoder on the same frames, on both serving kernels (the one
-specialised to the server's codes and the precompiled one), and the admission honours
-the HBM budget (queueing, never dropping)."""
+to the batch hybrid decoder on the same frames and to the oracle's hybrid decoder on
+every unambiguous frame, on both serving kernels (the one specialised to the server's
+codes and the precompiled one), and the admission honours the HBM budget (queueing,
+never dropping)."""
 import numpy as np
 import pytest
 
 import oracle as O
-from helpers import autos_dev, frames, to_dev
+from helpers import ambiguous_frames, autos_dev, frames, to_dev
 from paper_2412_20828_gb300 import bchdec as B
 
 pytestmark = pytest.mark.gpu
@@ -72,6 +73,7 @@ def test_results_alone_and_in_mix_match_batch_decoder(setup, monkeypatch, kernel
         # all at once, mixed
         rids = [srv.submit(code_id, llr, seed, f0) for code_id, llr, seed, f0 in reqs]
         mixed = _drain(srv, rids)
+        checked = 0
         for (code_id, llr, seed, f0), a, rid in zip(reqs, alone, rids):
             m = mixed[rid]
             for x, y in zip(a, m):
@@ -79,6 +81,17 @@ def test_results_alone_and_in_mix_match_batch_decoder(setup, monkeypatch, kernel
             ref = _batch_reference(torch, monkeypatch, codes[code_id], stds[code_id], llr, seed, f0)
             for x, y in zip(a, ref):
                 assert np.array_equal(x, y)
+            # and the oracle's hybrid decoder (Sec. IV) on every unambiguous frame
+            n = codes[code_id].n
+            autos = O.draw_autos(n, 3, seed, f0, llr.shape[0])
+            tr = O.nms_enhanced(codes[code_id].dense(), llr, autos, 12, 0.78, trace=True)
+            ok = ~ambiguous_frames(llr, tr, n)
+            hyb = O.hybrid(codes[code_id].dense(), stds[code_id].dense(), llr, autos, 12, 0.78)
+            assert np.array_equal(B.unpack_bits(a[0], n)[ok], hyb["final"][ok])
+            assert np.array_equal(a[1][ok], tr["iters"][ok])
+            assert np.array_equal((a[2] & B.FLAG_OSD)[ok] > 0, (tr["converged"][ok] == 0))
+            checked += int(ok.sum())
+        assert checked > 0.9 * sum(r[1].shape[0] for r in reqs)
         st = srv.stats()
         assert st["completed"] == 2 * len(reqs) and st["bytes_in_use"] == 0
     finally:

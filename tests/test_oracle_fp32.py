@@ -124,3 +124,24 @@ def test_fp32_range_renormalisation_is_exact():
     ok = ~ambiguous_frames(llr, ref, n)
     assert np.array_equal(r32["hard"][ok], ref["hard"][ok])
     assert drift(r32["y"], ref["y"], frame_envelope(ref)[:, None])[ok].max() < 1e-2
+
+
+def test_drift_table_matches_a_fresh_measurement():
+    # tests/golden/fp32_drift.txt (written by make_fp32_drift.py from the oracle) bounds
+    # the restatement's drift on a fresh, smaller sample of the same workloads, and the
+    # 12-iteration entry is reached within a factor 100 (the table is not vacuous; a
+    # sample's largest drift sits in a heavy tail, so smaller samples reach less of it)
+    from helpers import drift_table
+    tab = drift_table()
+    alpha = np.linspace(0.7, 0.9, 12)
+    worst = 0.0
+    for n, k in [(63, 36), (127, 99)]:
+        Ho = O.build_ho(n, k)
+        _, llr = frames(n, k, 300, 3.5, 200 + n + k, ld=(n + 3) & ~3)
+        autos = O.draw_autos(n, 3, 11, 0, 300)
+        ref = O.nms_enhanced(Ho, llr, autos, 12, alpha, trace=True, threads=None)
+        r32 = O.nms_enhanced_f32(Ho, llr, autos, 12, alpha, threads=None)
+        ok = ~ambiguous_frames(llr, ref, n)
+        worst = max(worst, drift(r32["y"], ref["y"], frame_envelope(ref)[:, None])[ok].max())
+    assert tab[("enhanced", 12)] / 100 <= worst <= tab[("enhanced", 12)]
+    assert tab[("enhanced", 12)] < tab[("enhanced", 32)]

@@ -41,6 +41,9 @@ def test_noalloc_matches_workspace_entry_point():
     ref = O.nms_enhanced(code.dense(), llr, autos, 12, 0.78, trace=True, threads=None)
     ok = ~ambiguous_frames(llr, ref, n)
     assert ok.mean() > 0.9
+    # the hybrid decoder of the oracle (Sec. IV): NMS word where its syndrome is zero,
+    # else the order-2 OSD word
+    hyb = O.hybrid(code.dense(), std.dense(), llr, autos, 12, 0.78, threads=None)
     for _ in range(2):  # two calls in a row on the shared scratch
         h1, i1, f1 = outputs()
         B.hybrid_decode_noalloc(code, std, p, d_llr, d_aut, h1, i1, f1)
@@ -48,6 +51,17 @@ def test_noalloc_matches_workspace_entry_point():
         assert np.array_equal(h1.cpu().numpy()[ok], h0.cpu().numpy()[ok])
         assert np.array_equal(i1.cpu().numpy()[ok], i0.cpu().numpy()[ok])
         assert np.array_equal(f1.cpu().numpy()[ok], f0.cpu().numpy()[ok])
+        words = B.unpack_bits(h1.cpu().numpy(), n)
+        assert np.array_equal(words[ok], hyb["final"][ok])
+        assert np.array_equal(i1.cpu().numpy()[ok], hyb["iters"][ok])
+    # a rejected call (OSD order 3) writes nothing: every check precedes the first launch
+    h2 = torch.full((F, 1), 7, dtype=torch.int64, device="cuda")
+    with pytest.raises(B.BchError) as e:
+        B.hybrid_decode_noalloc(code, std, B.params(12, 0.78, osd_order=3), d_llr, d_aut, h2,
+                                None, torch.zeros(F, dtype=torch.uint8, device="cuda"))
+    assert e.value.status == B.EINVAL
+    torch.cuda.synchronize()
+    assert bool((h2 == 7).all())
     # beyond the scratch limit: a clear error, nothing launched
     big = torch.zeros((262145, 64), dtype=torch.float32, device="cuda")
     with pytest.raises(B.BchError) as e:
