@@ -21,6 +21,9 @@ bool jit_compile_check(const bch_code *c, int msg, std::string *log);
 bool jit_serve_compile_check(const bch_code *const *codes, int n_codes, std::string *log);
 int jit_block_size(int n);
 int jit_scratch_words(int n);
+bool jit_split(int n);
+int jit_split_groups();
+int jit_split_chunk_rows();
 size_t nms_table_bytes_host(const DevCode &dc);
 }  // namespace bchlib
 
@@ -512,8 +515,15 @@ static cudaError_t launch_jit(cudaKernel_t k, const bch_code *code, const NmsArg
   const int n = code->alg.n, tpb = jit_block_size(n), scr = jit_scratch_words(n);
   const size_t sa = a.msg == BCH_MSG_INT8 ? 4 : 4;
   const size_t sy = a.msg == BCH_MSG_FP32 ? 4 : (a.msg == BCH_MSG_FP16 ? 2 : 1);
-  const size_t smem = nms_table_bytes_host(code->dc) + 16 +
-                      size_t(tpb) * (size_t(a.P) * 4 + size_t(n) * (sa + sy) + size_t(scr) * sa);
+  size_t smem = nms_table_bytes_host(code->dc) + 16 +
+                size_t(tpb) * (size_t(a.P) * 4 + size_t(n) * (sa + sy) + size_t(scr) * sa);
+  if (jit_split(n)) {  // two warps per 32 frames (see nms_split_persistent)
+    const int G = jit_split_groups(), R = jit_split_chunk_rows();
+    const size_t st = a.msg == BCH_MSG_FP32   ? SplitSmem<kFP32>::state_bytes(n, a.P, G, R)
+                      : a.msg == BCH_MSG_FP16 ? SplitSmem<kFP16>::state_bytes(n, a.P, G, R)
+                                              : SplitSmem<kINT8>::state_bytes(n, a.P, G, R);
+    smem = nms_table_bytes_host(code->dc) + st;
+  }
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   const void *fn = reinterpret_cast<const void *>(k);
   int sms = 0, per_sm = 0;
@@ -521,7 +531,8 @@ static cudaError_t launch_jit(cudaKernel_t k, const bch_code *code, const NmsArg
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long blocks = (long long)sms * per_sm;
-  const long long need = (a.F + tpb - 1) / tpb;
+  const int fpb = jit_split(n) ? tpb / 2 : tpb;  // frames a block holds at a time
+  const long long need = (a.F + fpb - 1) / fpb;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   void *args[] = {const_cast<NmsArgs *>(&a)};

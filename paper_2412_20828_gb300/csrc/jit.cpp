@@ -142,6 +142,32 @@ const char *row_macros(int msg) {
 )";
 }
 
+// Macros of the split mapping (two warps per 32 frames, each owning half of the
+// variables): BCH_PS stores the half's partial (min1 with the sign parity in its sign
+// bit, min2) of row r into buffer B; BCH_Q combines both halves' partials of row r into
+// m1_, m2_ and the row's sign parity sgp_ (inside a BCH_R0 block).
+const char *split_macros(int msg) {
+  if (msg == 2)
+    return R"(
+#define BCH_PS(B, r, SG) B[((r) * 2 + BCH_H) * BCH_FS] = \
+  make_float2(__int_as_float(m1_ | int(uint32_t(SG) << 31)), __int_as_float(m2_));
+#define BCH_Q(B, r) const float2 qa_ = B[((r) * 2) * BCH_FS], qb_ = B[((r) * 2 + 1) * BCH_FS]; \
+  const int xa_ = __float_as_int(qa_.x), xb_ = __float_as_int(qb_.x); \
+  const int a1_ = xa_ & 0x7fffffff, b1_ = xb_ & 0x7fffffff; \
+  m1_ = min(a1_, b1_); m2_ = min(max(a1_, b1_), min(__float_as_int(qa_.y), __float_as_int(qb_.y))); \
+  const uint32_t sgp_ = uint32_t(xa_ ^ xb_) >> 31;
+)";
+  return R"(
+#define BCH_PS(B, r, SG) B[((r) * 2 + BCH_H) * BCH_FS] = \
+  make_float2(__uint_as_float(__float_as_uint(m1_) | (uint32_t(SG) << 31)), m2_);
+#define BCH_Q(B, r) const float2 qa_ = B[((r) * 2) * BCH_FS], qb_ = B[((r) * 2 + 1) * BCH_FS]; \
+  const uint32_t xa_ = __float_as_uint(qa_.x), xb_ = __float_as_uint(qb_.x); \
+  const float a1_ = __uint_as_float(xa_ & 0x7fffffffu), b1_ = __uint_as_float(xb_ & 0x7fffffffu); \
+  m1_ = fminf(a1_, b1_); m2_ = fminf(fmaxf(a1_, b1_), fminf(qa_.y, qb_.y)); \
+  const uint32_t sgp_ = (xa_ ^ xb_) >> 31;
+)";
+}
+
 struct Compiled {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kernel = nullptr;
@@ -162,13 +188,20 @@ int env_int(const char *name, int lo, int hi, int dflt) {
 }
 }  // namespace
 
+// n = 127: the split mapping (two warps per 32 frames, half of the variables each, no
+// spills) unless BCHDEC_JIT_SPLIT=0 selects the one-thread-per-frame kernel (a tuning
+// and comparison knob; both compute identical results).
+bool jit_split(int n) { return n > 63 && env_int("BCHDEC_JIT_SPLIT", 0, 1, 1) == 1; }
+int jit_split_groups() { return 4; }      // 32-frame groups per block: 256 threads
+int jit_split_chunk_rows() { return 16; } // rows per partial exchange
+
 // Threads per block: 256 for n <= 63 (two warps per scheduler, all in lockstep so the
 // straight-line body is fetched once per block; 255 registers hold the 2n
 // register-resident values without spilling), 64 for n = 127.  BCHDEC_JIT_TPB (a
 // multiple of 32, 64..512) overrides it for n <= 63 -- a tuning knob.  Measured on the
 // (63,36) + (63,45) workload: 256 threads 187.1 M frames/s, 384 threads 186.0.
 int jit_block_size(int n) {
-  if (n > 63) return 64;
+  if (n > 63) return jit_split(n) ? 64 * jit_split_groups() : 64;
   const int t = env_int("BCHDEC_JIT_TPB", 64, 512, 256);
   return t % 32 == 0 ? t : 256;
 }
@@ -189,9 +222,9 @@ int jit_min_blocks(int n) {
   const char *v = std::getenv("BCHDEC_JIT_MIN_BLOCKS");  // tuning knob (register budget)
   if (v && std::atoi(v) >= 1 && std::atoi(v) <= 8) return std::atoi(v);
   if (n <= 63) return std::max(1, 384 / jit_block_size(n));
-  return 2;
+  return jit_split(n) ? 1 : 2;
 }
-int jit_scratch_words(int n) { return n <= 63 ? 0 : n; }
+int jit_scratch_words(int n) { return n <= 63 || jit_split(n) ? 0 : n; }
 
 // Common prologue of the generated sources: fixed-width types, the embedded device
 // headers, the three-input minimum and the row macros of one storage format.
@@ -306,7 +339,108 @@ static void emit_serve_copy(std::ostringstream &o, const bch_code *c, const std:
   o << "}\n";
 }
 
+// One half of the split mapping's automorphism copy: gather the half's 64 (or 63)
+// values of z_p, for every chunk of R rows the first pass over the half's columns
+// (partials to buffer A or B), a barrier, the second pass (combine, output pass), and
+// finally scatter the half's row sums.  Both halves are emitted from the same chunk
+// list, so they pass the same barriers.
+static void emit_split_half(std::ostringstream &o, const bch_code *c, int msg, int h, int R) {
+  const int n = c->alg.n, m = c->alg.m;
+  const int u0 = 64 * h, u1 = std::min(n, 64 * h + 64), nh = u1 - u0;
+  const int nwh = (nh + 31) / 32;
+  o << "__device__ " << (std::getenv("BCHDEC_JIT_SPLIT_NOINLINE") ? "__noinline__" : "__forceinline__") << " void split_half" << h << "(StoreT<" << msg << ">::Y *y, StoreT<" << msg
+    << ">::A *acc, float2 *pa, float2 *pb, uint32_t jr, uint32_t sp, float alpha) {\n"
+    << "#undef BCH_SV\n#define BCH_SV(u) S[u]\n#undef BCH_H\n#define BCH_H " << h << "\n"
+    << "  BCH_VT z[" << nh << "];\n"
+    << "#pragma unroll\n  for (int u = 0; u < " << nh << "; u++) {\n"
+    << "    const uint32_t uu = uint32_t(u + " << u0 << ");\n"
+    << "    const uint32_t i = addmod(bfe32(uu | (uu << " << m << "), jr, " << m << "), sp, " << n << ");\n"
+    << "    z[u] = ld_y(y + i * BCH_FS);\n  }\n"
+    << "  StoreT<" << msg << ">::A S[" << nh << "];\n#pragma unroll\n  for (int u = 0; u < " << nh
+    << "; u++) S[u] = 0;\n"
+    << "  uint32_t ng[" << nwh << "];\n#pragma unroll\n  for (int w = 0; w < " << nwh << "; w++) ng[w] = 0u;\n"
+    << "#pragma unroll\n  for (int u = 0; u < " << nh << "; u++) ng[u >> 5] |= "
+    << (msg == 2 ? "(uint32_t(z[u]) >> 31)" : "(__float_as_uint(z[u]) >> 31)") << " << (u & 31);\n";
+  // the half's columns (local indices) and its sign-parity expression, per row
+  const int M = int(c->rows.size());
+  std::vector<std::vector<int>> cols(M);
+  std::vector<std::string> par(M);
+  for (int r = 0; r < M; r++) {
+    uint32_t mw[2] = {0, 0};
+    for (int u = u0; u < u1; u++)
+      if (c->rows[r].get(u)) {
+        cols[r].push_back(u - u0);
+        mw[(u - u0) >> 5] |= 1u << ((u - u0) & 31);
+      }
+    std::ostringstream sg;
+    if (!mw[0] && !mw[1]) {
+      sg << "0u";
+    } else {
+      sg << "(__popc(";
+      bool first = true;
+      for (int w = 0; w < 2; w++) {
+        if (!mw[w]) continue;
+        if (!first) sg << " ^ ";
+        sg << "(ng[" << w << "] & 0x" << std::hex << mw[w] << std::dec << "u)";
+        first = false;
+      }
+      sg << ") & 1u)";
+    }
+    par[r] = sg.str();
+  }
+  const int nchunk = (M + R - 1) / R;
+  auto pass1 = [&](int ch) {
+    const char *buf = (ch & 1) ? "pb" : "pa";
+    for (int r = ch * R; r < std::min(M, ch * R + R); r++) {
+      o << "  BCH_R0";
+      for (int u : cols[r]) o << " BCH_R1(" << u << ")";
+      o << " BCH_PS(" << buf << ", " << (r - ch * R) << ", " << par[r] << ") BCH_RE\n";
+    }
+  };
+  auto pass2 = [&](int ch) {
+    const char *buf = (ch & 1) ? "pb" : "pa";
+    for (int r = ch * R; r < std::min(M, ch * R + R); r++) {
+      if (cols[r].empty()) continue;  // no edge of this half: nothing to add
+      o << "  BCH_R0 BCH_Q(" << buf << ", " << (r - ch * R) << ") BCH_RM(sgp_)";
+      for (int u : cols[r]) o << " BCH_R2(" << u << ")";
+      o << " BCH_RE\n";
+    }
+  };
+  pass1(0);
+  for (int ch = 0; ch < nchunk; ch++) {
+    o << "  bar_block(BCH_TPB);\n";
+    pass2(ch);
+    if (ch + 1 < nchunk) pass1(ch + 1);
+  }
+  o << "#pragma unroll\n  for (int u = 0; u < " << nh << "; u++) {\n"
+    << "    const uint32_t uu = uint32_t(u + " << u0 << ");\n"
+    << "    const uint32_t i = addmod(bfe32(uu | (uu << " << m << "), jr, " << m << "), sp, " << n << ");\n"
+    << "    acc[i * BCH_FS] += BCH_FIN(u);\n  }\n}\n";
+}
+
+static std::string jit_split_source(const bch_code *c, int msg) {
+  const int G = jit_split_groups(), R = jit_split_chunk_rows();
+  const int M = int(c->rows.size());
+  std::ostringstream o;
+  emit_prologue(o, msg, false);
+  o << split_macros(msg) << "#define BCH_FS " << 32 * G << "\n#define BCH_TPB " << 64 * G << "\n";
+  emit_split_half(o, c, msg, 0, R);
+  emit_split_half(o, c, msg, 1, R);
+  o << "struct SplitCopy {\n"
+    << "  __device__ __forceinline__ void operator()(int h, StoreT<" << msg << ">::Y *y, StoreT<" << msg
+    << ">::A *acc,\n      float2 *pa, float2 *pb, uint32_t jr, uint32_t sp, float alpha) const {\n"
+    << "    if (h == 0) split_half0(y, acc, pa, pb, jr, sp, alpha);\n"
+    << "    else split_half1(y, acc, pa, pb, jr, sp, alpha);\n  }\n};\n"
+    << "}  // namespace bchlib\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << 64 * G << ", 1) bch_nms_jit(const bchlib::NmsArgs a) {\n"
+    << "  extern __shared__ __align__(16) unsigned char smem[];\n"
+    << "  bchlib::nms_split_persistent<" << msg << ", " << G << ">(a, smem, bchlib::SplitCopy(), "
+    << (M + R - 1) / R << ", " << R << ");\n}\n";
+  return o.str();
+}
+
 std::string jit_source(const bch_code *c, int msg) {
+  if (jit_split(c->alg.n)) return jit_split_source(c, msg);
   const int n = c->alg.n;
   const int tpb = jit_block_size(n);
   const int nw = (n + 31) / 32;
@@ -421,8 +555,9 @@ cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err
 // The tuning knobs that shape the generated source (read from the environment).
 static std::string jit_knob_signature(int n) {
   char buf[96];
-  std::snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d", jit_block_size(n), jit_min_blocks(n), int(jit_pairs()),
-                jit_fma_percent(), env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, 0), jit_scratch_words(n));
+  std::snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d", jit_block_size(n), jit_min_blocks(n), int(jit_pairs()),
+                jit_fma_percent(), env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, 0), jit_scratch_words(n),
+                int(jit_split(n)));
   return buf;
 }
 

@@ -499,6 +499,212 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
 }
 
 
+// ---------------------------------------------------------------- split mapping (n = 127)
+// Two warps share 32 frames: warp half h owns the variables [64h, 64h + 64) of every
+// automorphism copy (its 64 values of z and of the row sums S stay in registers, as in
+// the n <= 63 kernel), and of the frame's own positions for the merge.  A check row
+// spans both halves: each half reduces its own columns to (min1, min2, sign parity),
+// publishes that partial in shared memory, and after a block barrier combines it with
+// the other half's -- min1 = min(a1, b1), min2 = min(max(a1, b1), a2, b2), parity
+// a ^ b -- before its output pass.  Rows go in chunks of R with one barrier per
+// chunk; partials alternate between two buffers, so the first pass of chunk c + 1 can
+// run before the other half has read chunk c.  Row order and every addition are those
+// of the one-thread-per-frame kernel, so the results are bit-identical to it.
+//
+// The barrier inside a copy is a named barrier over the whole block, reached by the two
+// halves at different code locations (each half runs its own straight-line copy); both
+// copies are emitted from one chunk list, so they pass the same number of barriers.
+__device__ __forceinline__ void bar_block(unsigned nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Per-block shared-memory layout of the split kernel: tables, then (per frame slot,
+// Fs = 32 G slots, element [x][slot] at x * Fs + slot) ctx[2][P], acc[n], y[n],
+// partials[2 buffers][R rows][2 halves] (float2), the merge exchange and the frame
+// hand-off aliasing the partial buffers (unused between the copies).
+template <int MSG>
+struct SplitSmem {
+  static __host__ __device__ size_t state_bytes(int n, int P, int G, int R) {
+    const size_t Fs = size_t(32) * G;
+    const size_t ya = sizeof(typename StoreT<MSG>::Y);
+    size_t b = Fs * 4 * 2 * size_t(P);                    // ctx, one copy per half
+    b += Fs * 4 * size_t(n);                              // acc (FP32 / int32)
+    b += (Fs * ya * size_t(n) + 15) & ~size_t(15);        // y
+    b += Fs * 8 * 2 * 2 * size_t(R);                      // partials
+    return b;
+  }
+};
+
+template <int MSG, int G, class Copy>
+__device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned char *smem, const Copy &copy,
+                                                     int nchunk, int R) {
+  using Y = typename StoreT<MSG>::Y;
+  using A = typename StoreT<MSG>::A;
+  constexpr int Fs = 32 * G, TPB = 64 * G;
+  const int code_words = a.dc.group_off[a.dc.n_groups];
+  SmemTables tb = load_tables(a, smem, code_words);
+  const int n = a.dc.n;
+  const uint32_t m = uint32_t(a.dc.m);
+  const int warp = int(threadIdx.x >> 5), lane = int(lane_id());
+  // Warp w issues from scheduler w % 4.  Half 0 takes the warps with (w >> 1) even,
+  // half 1 the others, so each scheduler runs warps of one half only -- one stream of
+  // straight-line copy code per scheduler, shared by its lockstep warps.
+  const int h = (warp >> 1) & 1;                               // half of the variables
+  const int s = ((warp & 1) + ((warp >> 2) << 1)) * 32 + lane;  // frame slot (G = 4)
+  static_assert(G == 4, "the warp-to-half map assumes 8 warps per block");
+  const int i0 = h * 64, i1 = h ? n : (n < 64 ? n : 64);
+  uint32_t *ctx = reinterpret_cast<uint32_t *>(tb.state) + size_t(h) * a.P * Fs + s;
+  A *acc_s = reinterpret_cast<A *>(tb.state + size_t(Fs) * 4 * 2 * a.P);
+  Y *y_s = reinterpret_cast<Y *>(reinterpret_cast<unsigned char *>(acc_s) + size_t(Fs) * 4 * n);
+  unsigned char *pbase = reinterpret_cast<unsigned char *>(y_s) +
+                         ((size_t(Fs) * sizeof(Y) * n + 15) & ~size_t(15));
+  float2 *part = reinterpret_cast<float2 *>(pbase);
+  uint4 *xch = reinterpret_cast<uint4 *>(pbase);                       // [2][Fs], merge exchange
+  int *fslot = reinterpret_cast<int *>(pbase + size_t(Fs) * 16 * 2);   // [Fs], frame hand-off
+  A *acc = acc_s + s;
+  Y *y = y_s + s;
+  const float invP = 1.0f / float(a.P);
+  const bool vec = ((a.ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.llr) & 15) == 0);
+  for (int p = 0; p < a.P; p++) ctx[p * Fs] = 0u;  // idle slots run copies on valid maps
+
+  int f = -1, t = 0, escale = 0;
+  bool need = true;
+  for (;;) {
+    // half 0 pulls the slot's next frame and hands it to half 1
+    if (h == 0) {
+      const int got = pull_frame(a.queue, need, a.F);
+      if (need) fslot[s] = got;
+    }
+    bar_block(TPB);
+    if (need) {
+      need = false;
+      f = fslot[s];
+      if (f >= 0) {
+        t = 0;
+        escale = 0;
+        const float *src = a.llr + size_t(f) * a.ld;
+        for (int i = i0; i < i1; i += 4) {
+          float4 v;
+          if (vec) {
+            v = __ldg(reinterpret_cast<const float4 *>(src + i));
+          } else {
+            v.x = src[i];
+            v.y = i + 1 < n ? src[i + 1] : 0.f;
+            v.z = i + 2 < n ? src[i + 2] : 0.f;
+            v.w = i + 3 < n ? src[i + 3] : 0.f;
+          }
+          const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            if (i + q < i1) {
+              const float x = vv[q] + 0.0f;  // -0 -> +0: sgn(0) = +1
+              if constexpr (MSG == kFP32) y[(i + q) * Fs] = x;
+              if constexpr (MSG == kFP16) y[(i + q) * Fs] = to_half_sat(x);
+              if constexpr (MSG == kINT8) y[(i + q) * Fs] = to_q(4.0f * x);
+              acc[(i + q) * Fs] = A(0);
+              if (a.ckpt) a.ckpt[size_t(f) * a.ld + i + q] = x;
+            }
+          }
+        }
+        for (int p = 0; p < a.P; p++) {
+          const uint32_t v = a.autos[size_t(f) * a.P + p];
+          const uint32_t sh = v & 0xffu, j = v >> 8;
+          const uint32_t rs = j ? (((sh >> j) | (sh << (m - j))) & uint32_t(n)) : sh;
+          ctx[p * Fs] = j | ((rs ? uint32_t(n) - rs : 0u) << 8);
+        }
+      }
+    }
+    if (!__syncthreads_or(f >= 0)) break;
+
+    const float alpha = tb.alpha[f >= 0 ? t : 0];
+    for (int p = 0; p < a.P; p++) {
+      const uint32_t cx = f >= 0 ? ctx[p * Fs] : 0u;
+      // the partial buffers alternate across the copies' chunks too
+      float2 *pa = part + (((p * nchunk) & 1) ? size_t(2) * R * Fs : 0) + s;
+      float2 *pb = part + (((p * nchunk) & 1) ? 0 : size_t(2) * R * Fs) + s;
+      copy(h, y, acc, pa, pb, cx & 0xffu, cx >> 8, alpha);
+    }
+    __syncthreads();  // every copy's accumulation is in acc
+
+    // merge of this half's positions (FP32), its hard-decision bits and magnitude
+    uint32_t cw0 = 0, cw1 = 0;
+    float mx = 0.0f;
+    const float fP = float(a.P);
+    for (int i = i0; i < i1; i++) {
+      float yn;
+      if constexpr (MSG == kFP32) {
+        yn = __fmaf_rn(acc[i * Fs], invP, y[i * Fs]);
+        y[i * Fs] = yn;
+      } else if constexpr (MSG == kINT8) {
+        yn = float(ld_y(y + i * Fs)) + __fdiv_rn(float(acc[i * Fs]), fP);
+        reinterpret_cast<float *>(acc)[i * Fs] = yn;
+      } else {
+        yn = __fmaf_rn(ld_y(y + i * Fs), fP, acc[i * Fs]);
+        reinterpret_cast<float *>(acc)[i * Fs] = yn;
+      }
+      if constexpr (MSG == kFP32) acc[i * Fs] = 0.0f;
+      const uint32_t b = (__float_as_uint(yn) >> 31) << ((i - i0) & 31);
+      if (i - i0 < 32) cw0 |= b; else cw1 |= b;
+      mx = fmaxf(mx, fabsf(yn));
+    }
+    xch[h * Fs + s] = make_uint4(cw0, cw1, __float_as_uint(mx), 0u);
+    __syncthreads();
+    const uint4 o = xch[(1 - h) * Fs + s];
+    uint32_t cb[4];
+    cb[h * 2] = cw0;
+    cb[h * 2 + 1] = cw1;
+    cb[(1 - h) * 2] = o.x;
+    cb[(1 - h) * 2 + 1] = o.y;
+    mx = fmaxf(mx, __uint_as_float(o.z));
+    if constexpr (MSG == kFP32) {
+      // exact power-of-two renormalisation past 2^100 (as in the one-thread kernel)
+      if (mx > 0x1p100f && !a.ckpt && f >= 0) {
+        for (int i = i0; i < i1; i++) y[i * Fs] *= 0x1p-64f;
+        escale += 64;
+      }
+    } else {
+      float sc = 1.0f;
+      if (a.rescale) {
+        const float lim = (MSG == kINT8) ? 31.0f : 16384.0f * fP;
+        int k = 0;
+        while (mx * sc > lim && k < 126) {
+          sc *= 0.5f;
+          k++;
+        }
+        escale += k;
+      }
+      for (int i = i0; i < i1; i++) {
+        const float yn = reinterpret_cast<float *>(acc)[i * Fs] * sc;
+        if constexpr (MSG == kINT8)
+          y[i * Fs] = to_q(yn);
+        else
+          y[i * Fs] = half_of_quotient(yn, fP);
+        acc[i * Fs] = A(0);
+      }
+    }
+    if (f < 0) continue;
+    t++;
+    if (a.ckpt) {
+      float *dst = a.ckpt + (size_t(t) * a.F + f) * a.ld;
+      for (int i = i0; i < i1; i++) dst[i] = float(ld_y(y + i * Fs));
+    }
+    const uint32_t nz = syndrome_nonzero<4>(tb.rowmask, a.dc.rows, cb);
+    if (t >= a.I || (a.early_stop && nz == 0)) {
+      if (h == 0) {
+        if (a.hard) write_hard<4>(a.hard, f, cb);
+        if (a.iters) a.iters[f] = uint8_t(t);
+        if (a.flags) a.flags[f] = nz ? 0 : uint8_t(kFlagConverged);
+      }
+      if (a.llr_out) {
+        float *dst = a.llr_out + size_t(f) * a.ld;
+        const float unit = MSG == kINT8 ? 0.25f : 1.0f;
+        for (int i = i0; i < i1; i++) dst[i] = ldexpf(float(ld_y(y + i * Fs)) * unit, escale);
+      }
+      need = true;
+    }
+  }
+}
+
 // Precompiled path: rows read their column codes from shared memory.
 template <int MSG, int WB>
 struct GenericCopy {
