@@ -42,6 +42,11 @@ LANE_OPS_PER_EDGE = 8  # min1/min2 (3), sign (1), output select (2), accumulate 
 # LLRs are read once, its results written once), so a launch's traffic is this figure
 # times its frames.  Set to None when the kernel changes until it is re-captured.
 JIT_DRAM_BYTES_PER_FRAME = (288.36e6 + 10.23e6) / 1.1e6
+# The same for the n = 127 specialised kernel (split mapping), from one ncu capture of
+# a 400 000-frame BCH(127,64) launch at 3 dB: 208.75 MB + 7.82 MB.
+JIT127_DRAM_BYTES_PER_FRAME = (208.75e6 + 7.82e6) / 4e5
+CONFIG4_CODES = [(127, 64), (127, 99)]
+CONFIG4_POINTS = [2.0 + 0.5 * i for i in range(7)]
 
 
 def measured_peaks():
@@ -281,6 +286,113 @@ def run_plain(B, torch, dev, reps=50):
             "edge_updates_per_s": float(c[5]) * 486 / dt}
 
 
+def nms_roofline(B, torch, dev, clocks, edge_updates, nms_time, kinfo, frames, n, traffic_per_frame):
+    """Roofline of the enhanced-NMS kernel: ALU lane-ops (8 per edge update) per second
+    against SMs x 128 lanes x the median SM clock under load."""
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_lane_ops = sms * 128 * clk_mhz * 1e6
+    achieved = edge_updates * LANE_OPS_PER_EDGE / nms_time
+    traffic = None
+    if kinfo == "jit" and traffic_per_frame is not None:
+        traffic = traffic_per_frame * frames  # bytes per launch (one code's frames)
+    W64 = (n + 63) // 64
+    ld = 64 if n <= 63 else 128
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lane_ops / 1e12,
+            "unit": "Tlane-op/s", "frac": achieved / peak_lane_ops, "traffic": traffic,
+            "traffic_unit": "bytes per launch", "algorithmic_bytes_per_launch": frames * (n * 4 + W64 * 8 + 2),
+            "kernel": "bch_nms_jit" if kinfo == "jit" else "nms_enhanced_kernel", "kernel_info": kinfo,
+            "lane_ops_per_edge_update": LANE_OPS_PER_EDGE, "edge_updates_per_s": edge_updates / nms_time,
+            "nms_ms_per_step": nms_time * 1e3,
+            "peak_basis": f"{sms} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock under load)",
+            "ld": ld}
+
+
+def run_config4(B, torch, dev, clocks, frames_per_point, steps=2, warmup=1):
+    """Config 4: hybrid decoding of BCH(127,64) and BCH(127,99) on H_o (2(n-k) rows), P = 3,
+    12 iterations with early stop, order-2 OSD on the failed frames, Eb/N0 2.0 ... 5.0 dB
+    (7 points) x frames_per_point frames per point and code, generated on the device
+    before timing.  One step decodes every frame of both codes (the config-2 step's
+    sequence); the NMS launches are timed with CUDA events for the n = 127 kernel's
+    roofline."""
+    Bp, NPT = frames_per_point, len(CONFIG4_POINTS)
+    F = Bp * NPT
+    stream = torch.cuda.current_stream()
+    states = []
+    for (n, k) in CONFIG4_CODES:
+        code, std = B.Code(n, k), B.Code(n, k, kind=B.PCM_STANDARD)
+        p = B.params(ITERS, ALPHA, n_autos=P_AUTOS, osd_order=OSD_ORDER)
+        llr = torch.empty((F, 128), dtype=torch.float32, device=dev)
+        cw = torch.empty((F, 2), dtype=torch.int64, device=dev)
+        for pi, e in enumerate(CONFIG4_POINTS):
+            B.gen_frames(code, e, e, SEED_FRAMES + 4, pi * 10_000_000, llr[pi * Bp:(pi + 1) * Bp],
+                         cw[pi * Bp:(pi + 1) * Bp])
+        states.append(dict(n=n, k=k, code=code, std=std, p=p, llr=llr, cw=cw,
+                           autos=torch.empty((F, P_AUTOS), dtype=torch.int16, device=dev),
+                           hard=torch.empty((F, 2), dtype=torch.int64, device=dev),
+                           iters=torch.empty(F, dtype=torch.uint8, device=dev),
+                           flags=torch.empty(F, dtype=torch.uint8, device=dev),
+                           lst=torch.empty(F, dtype=torch.int32, device=dev),
+                           cnt=torch.empty(1, dtype=torch.int32, device=dev),
+                           ctr=torch.zeros((NPT, 8), dtype=torch.int64, device=dev),
+                           ws=B.workspace(code, p, F, device=dev), ev=[]))
+
+    def step(record):
+        for st in states:
+            st["ctr"].zero_()
+            for pi in range(NPT):
+                B.draw_automorphisms(st["n"], P_AUTOS, SEED_AUTOS, pi * 10_000_000,
+                                     st["autos"][pi * Bp:(pi + 1) * Bp])
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.nms_decode(st["code"], st["p"], st["llr"], st["autos"], st["hard"], st["iters"],
+                         st["flags"], None, st["ws"])
+            b.record(stream)
+            if record:
+                st["ev"].append((a, b))
+            B.compact_failed(st["flags"], st["lst"], st["cnt"], st["ws"])
+            B.osd_decode(st["std"], OSD_ORDER, st["llr"], st["lst"], st["cnt"], st["hard"], st["flags"],
+                         st["ws"])
+            for pi in range(NPT):
+                sl = slice(pi * Bp, (pi + 1) * Bp)
+                B.count_errors(st["n"], st["hard"][sl], st["cw"][sl], st["iters"][sl], st["flags"][sl],
+                               st["ctr"][pi])
+
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    dt = t0.elapsed_time(t1) / 1e3 / steps
+    out = {"workload": "BCH(127,64)+BCH(127,99) on H_o (2(n-k) rows), P=3, 12 iters early stop, "
+                       "Eb/N0 2..5 dB step 0.5, hybrid OSD(2) fallback",
+           "frames_per_point": Bp, "points": NPT, "frames_per_step": 2 * F, "steps": steps,
+           "ms_per_step": dt * 1e3, "frames_per_s": 2 * F / dt, "codes": {}}
+    for st in states:
+        nms_t = sum(a.elapsed_time(b) for a, b in st["ev"]) / 1e3 / steps
+        ctr = st["ctr"].cpu().numpy()
+        eu = int(ctr[:, 5].sum()) * P_AUTOS * st["code"].edges
+        kinfo = st["code"].kernel_info(B.MSG_FP32, P_AUTOS)
+        pts = []
+        for pi, e in enumerate(CONFIG4_POINTS):
+            c = ctr[pi]
+            pts.append({"ebn0": e, "fer": c[1] / c[0], "fer_ci95": list(clopper_pearson(int(c[1]), int(c[0]))),
+                        "ber": c[2] / (c[0] * st["n"]), "nms_fer": 1 - c[6] / c[0],
+                        "avg_iters": c[5] / c[0], "osd_frames": int(c[4])})
+        out["codes"][f"({st['n']},{st['k']})"] = {
+            "roofline": nms_roofline(B, torch, dev, clocks, eu, nms_t, kinfo, F, st["n"],
+                                     JIT127_DRAM_BYTES_PER_FRAME if st["n"] == 127 else None),
+            "per_point": pts}
+        st["code"].close()
+        st["std"].close()
+    return out
+
+
 def run_training(B, torch, steps, batch=65536, iters=12):
     """BCH(127,64) enhanced NMS (P = 3), alpha_1..alpha_12 trained from 0.78 by Adam on
     batches of 65 536 frames at Eb/N0 uniform in [2, 5] dB that the library simulates,
@@ -319,6 +431,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the single-decoder leg")
     ap.add_argument("--train-steps", type=int, default=20,
                     help="Adam steps of the BCH(127,64) alpha_t training leg (0 skips it)")
+    ap.add_argument("--config4-frames-per-point", type=int, default=1_000_000,
+                    help="frames per point of the BCH(127,64)+BCH(127,99) hybrid leg (0 skips it)")
+    ap.add_argument("--msg-legs", default="fp16,int8",
+                    help="storage formats whose config-2 step is also timed ('' skips)")
     args = ap.parse_args()
 
     from paper_2412_20828_gb300 import dist as D
@@ -410,10 +526,12 @@ def main():
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    launches0 = B.kernel_launches()
     t_start.record(stream)
     for _ in range(args.steps):
         step(True)
     t_end.record(stream)
+    launches = B.kernel_launches() - launches0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -449,22 +567,39 @@ def main():
     ms = elapsed / args.steps * 1e3
     value = D.job_throughput(frames_per_step, world, elapsed / args.steps)
     eups = edge_updates / nms_time
-    peaks = measured_peaks()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_lane_ops = sms * 128 * clk_mhz * 1e6
-    achieved = edge_updates * LANE_OPS_PER_EDGE / nms_time
     kinfo = states[0]["code"].kernel_info(msg, P_AUTOS)
-    kname = "bch_nms_jit" if kinfo == "jit" else "nms_enhanced_kernel"
-    traffic = None
-    if kinfo == "jit" and JIT_DRAM_BYTES_PER_FRAME is not None:
-        traffic = JIT_DRAM_BYTES_PER_FRAME * F  # bytes per launch (one code, F frames)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lane_ops / 1e12,
-                "unit": "Tlane-op/s", "frac": achieved / peak_lane_ops, "traffic": traffic,
-                "traffic_unit": "bytes per launch", "algorithmic_bytes_per_launch": F * (63 * 4 + 6 + 10),
-                "kernel": kname, "kernel_info": kinfo, "lane_ops_per_edge_update": LANE_OPS_PER_EDGE,
-                "edge_updates_per_s": eups, "nms_ms_per_step": nms_time * 1e3,
-                "peak_basis": f"{sms} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock under load)"}
+    roofline = nms_roofline(B, torch, dev, clocks, edge_updates, nms_time, kinfo, F, 63,
+                            JIT_DRAM_BYTES_PER_FRAME if msg == B.MSG_FP32 else None)
+
+    # ---- the same step with reduced-precision message storage (throughput only)
+    msg_legs = {}
+    for name in [x for x in args.msg_legs.split(",") if x and x != args.msg]:
+        mv = {"fp32": B.MSG_FP32, "fp16": B.MSG_FP16, "int8": B.MSG_INT8}[name]
+        saved = [st["p"] for st in states]
+        for st in states:
+            st["p"] = B.params(ITERS, ALPHA, n_autos=P_AUTOS, early_stop=True, msg=mv, osd_order=OSD_ORDER)
+        step(False)  # compiles this format's kernels
+        torch.cuda.synchronize()
+        ev_nms.clear()
+        ms_steps = 2
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(ms_steps):
+            step(True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t_leg = a0.elapsed_time(a1) / 1e3 / ms_steps
+        nt = sum(a.elapsed_time(b) for a, b, _ in ev_nms) / 1e3 / ms_steps
+        eu = sum(int(st["iters"].long().sum()) * P_AUTOS * st["code"].edges for st in states)
+        fe = [int((st["hard"] != st["cw"]).any(dim=1).sum()) for st in states]
+        msg_legs[name] = {"frames_per_s": frames_per_step / t_leg, "ms_per_step": t_leg * 1e3,
+                          "roofline": nms_roofline(B, torch, dev, clocks, eu, nt,
+                                                   states[0]["code"].kernel_info(mv, P_AUTOS), F, 63, None),
+                          "frame_errors_per_code": fe}
+        for st, p0 in zip(states, saved):
+            st["p"] = p0
+        progress(f"{name} leg done")
+    ev_nms.clear()
 
     progress("device-timed steps done")
     # ---- end to end through the host pipeline (bch_decoder), copies inside the timing
@@ -473,7 +608,9 @@ def main():
         dec = []
         host = []
         for st in states:
-            dec.append(B.HostDecoder(st["code"], st["std"], st["p"], ld, chunk_frames=1 << 20))
+            # in place, chunks only size the automorphism and workspace buffers: one chunk
+            # per call gives one decode launch (one tail of slow frames) per code
+            dec.append(B.HostDecoder(st["code"], st["std"], st["p"], ld, chunk_frames=F))
             hl = torch.empty((F, ld), dtype=torch.float32, pin_memory=True)
             hl.copy_(st["llr"].cpu())
             hh = torch.empty((F, 1), dtype=torch.int64, pin_memory=True)
@@ -485,11 +622,11 @@ def main():
         for s in range(1 + e2e_steps):
             if s == 1:
                 torch.cuda.synchronize()
+                for d in dec:
+                    d.set_timing(True)
                 t0 = time.perf_counter()
-            # one call per code over all its frames: the pipeline overlaps each chunk's
-            # copy-in with the previous chunk's decode (automorphisms drawn from the
-            # frames' position in the call); 1M-frame chunks keep the number of decode
-            # launches, each ending in a tail of slow frames, small
+            # one call per code over all its frames (automorphisms drawn from the frames'
+            # position in the call)
             for ci, (d, (hl, hh, hi, hf), st) in enumerate(zip(dec, host, states)):
                 tc = time.perf_counter()
                 d.run(hl, SEED_AUTOS, st["base"], hh, hi, hf)
@@ -497,14 +634,51 @@ def main():
                     code_s[ci] += time.perf_counter() - tc
         t1 = time.perf_counter()
         e2e_v = frames_per_step * world / ((t1 - t0) / e2e_steps)
+        # device time of the pipeline's phases per code call (CUDA events per chunk):
+        # copies in, decode launches, copies out (in place: no copies)
+        phases = []
+        for d in dec:
+            t = d.timing()
+            phases.append({k: round(t[k] / max(1, t["calls"]), 2) for k in ("ms_wall", "ms_h2d", "ms_decode",
+                                                                           "ms_d2h")})
+        in_place = all(d.timing()["in_place_chunks"] == d.timing()["chunks"] for d in dec)
+        # the same calls with 1M-frame chunks staged through device buffers by copies on
+        # two streams (the path for pageable host memory), for comparison
+        for d in dec:
+            d.close()
+        dec = [B.HostDecoder(st["code"], st["std"], st["p"], ld, chunk_frames=1 << 20) for st in states]
+        for d in dec:
+            d.set_in_place(False)
+            d.run(host[0][0][:1 << 20], SEED_AUTOS, 0, host[0][1][:1 << 20])  # warm-up
+            d.set_timing(True)
+        torch.cuda.synchronize()
+        ts0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for d, (hl, hh, hi, hf), st in zip(dec, host, states):
+                d.run(hl, SEED_AUTOS, st["base"], hh, hi, hf)
+        staged_v = frames_per_step * world / ((time.perf_counter() - ts0) / e2e_steps)
+        staged_phases = []
+        for d in dec:
+            t = d.timing()
+            staged_phases.append({k: round(t[k] / max(1, t["calls"]), 2)
+                                  for k in ("ms_wall", "ms_h2d", "ms_decode", "ms_d2h")})
         e2e = {"value": e2e_v, "unit": "frames/s",
                "h2d_bytes_per_step": int(frames_per_step * ld * 4),
                "d2h_bytes_per_step": int(frames_per_step * (8 + 2)),
-               "ms_per_code_call": [round(x / e2e_steps * 1e3, 2) for x in code_s]}
+               "mode": "in place: the kernels read the pinned host LLRs and write the results to pinned "
+                       "host memory over the CPU-GPU link" if in_place else "staged copies",
+               "ms_per_code_call": [round(x / e2e_steps * 1e3, 2) for x in code_s],
+               "phases_per_code_call": phases,
+               "staged_copies": {"value": staged_v, "phases_per_code_call": staged_phases}}
         for d in dec:
             d.close()
 
     progress("end-to-end done")
+    # ---- config 4: hybrid decoding of the two n = 127 codes, own roofline
+    config4 = None
+    if rank == 0 and args.config4_frames_per_point > 0:
+        config4 = run_config4(B, torch, dev, clocks, args.config4_frames_per_point)
+        progress("config 4 done")
     # ---- serving: mixed-code Poisson stream, server vs static batching
     serving = None
     if rank == 0 and args.serve_seconds > 0:
@@ -590,7 +764,9 @@ def main():
                        "frames_per_step": frames_per_step, "l2": "inputs 5.6 GB > L2 (no flush)",
                        "parallelism": f"frames sharded over {world} GPU(s)"},
             "edge_updates_per_s": eups, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clocks, "gpu_launches": args.steps * len(CODES) * (NPT + 1 + 2 + 1 + NPT),
+            "clocks": clocks, "gpu_launches": launches,
+            "gpu_launches_basis": "library kernel launches counted (bch_kernel_launches) over the timed steps",
+            "msg_legs": msg_legs, "config4": config4,
             "serving": serving, "training": training, "plain_nms": plain,
             "fer_match_oracle_ci95": fer_match, "fer_match_detail": fer_detail, "per_point": per_point,
         }

@@ -79,6 +79,14 @@ typedef struct {
                           two after every merge; min-sum is scale invariant, so only
                           quantisation changes.  0: plain saturation                     */
   int osd_order;       /* hybrid decoding only: OSD order 0..2                            */
+  int osd_input;       /* hybrid decoding only: the reliabilities the OSD ranks and scores.
+                          0: the channel LLR, the magnitude of Eq. (1) (Sec. II-B).
+                          1: the frame's final NMS output y (the "improved" reliability
+                          measure Sec. II-B allows), scaled by the power of two that puts
+                          max_i |y_i| in [2^15, 2^16) -- exact, and the OSD's choice does
+                          not depend on a common scale -- so that its integer weights
+                          floor(|y| 2^24) resolve the values; needs llr_out, which
+                          receives y and which the OSD reads                             */
 } bch_nms_params;
 
 /* Per-frame flag bits written by the decoders. */
@@ -269,15 +277,36 @@ typedef struct bch_decoder bch_decoder;
 bch_status bch_decoder_create(const bch_code *code, const bch_code *std_code,
                               const bch_nms_params *params, int ld, int chunk_frames,
                               bch_decoder **out);
-/* Decodes n_frames frames from host memory: llr [n_frames][ld] FP32 (page-locked
- * memory gives full copy bandwidth), automorphisms drawn on the device from
- * (autos_seed, frame0 + index), results to host arrays hard [n_frames][ceil(n/64)],
- * iters and flags [n_frames] (iters/flags nullable).  Returns when all results are
- * in host memory. */
+/* Decodes n_frames frames from host memory: llr [n_frames][ld] FP32, automorphisms drawn
+ * on the device from (autos_seed, frame0 + index), results to host arrays hard
+ * [n_frames][ceil(n/64)], iters and flags [n_frames] (iters/flags nullable).  Returns
+ * when all results are in host memory.  When every buffer is page-locked host memory
+ * mapped into the device's address space (cudaHostAlloc, or torch's pin_memory, under
+ * unified addressing) the kernels read the LLRs and write the results in place -- on a
+ * GB300 over the coherent CPU-GPU link -- with no staging copies; otherwise (pageable
+ * memory, or bch_decoder_set_in_place(dec, 0)) each chunk is copied in and its results
+ * copied out on the two streams. */
 bch_status bch_decoder_run_host(bch_decoder *dec, const float *llr, int n_frames,
                                 uint64_t autos_seed, uint64_t frame0, uint64_t *hard,
                                 uint8_t *iters, uint8_t *flags);
 void bch_decoder_destroy(bch_decoder *dec);
+/* Per-phase timing of bch_decoder_run_host, a measurement aid with no counterpart in
+ * the paper.  bch_decoder_set_timing(dec, 1) clears the totals and makes every later
+ * run_host call record four CUDA events per chunk on the chunk's stream (around the
+ * copy-in, the decode and the copy-out) and its host wall time; set_timing(dec, 0)
+ * stops.  bch_decoder_get_timing returns the totals since the last set_timing: calls,
+ * chunks, ms_wall (host time inside run_host), and the device time of the copies in,
+ * of the decode launches (automorphism draw, NMS, compaction, OSD) and of the copies
+ * out.  The two streams overlap, so the three device sums can exceed ms_wall. */
+typedef struct {
+  long long calls, chunks, in_place_chunks; /* in_place_chunks: decoded without copies */
+  double ms_wall, ms_h2d, ms_decode, ms_d2h;
+} bch_decoder_timing;
+bch_status bch_decoder_set_timing(bch_decoder *dec, int on);
+/* 1 (default): decode mapped page-locked host buffers in place (see run_host); 0: always
+ * stage the chunks through the decoder's device buffers with copies. */
+bch_status bch_decoder_set_in_place(bch_decoder *dec, int on);
+bch_status bch_decoder_get_timing(const bch_decoder *dec, bch_decoder_timing *out);
 
 /* ---------------------------------------------------------------- serving */
 
@@ -417,6 +446,10 @@ bch_status bch_train_alpha(const bch_code *code, int n_autos, int iters, float *
 
 const char *bch_status_str(bch_status s);
 const char *bch_last_error(void);
+/* Number of kernels this library has launched in the process so far (every device and
+ * thread; incremented at each launch), e.g. to count the launches inside a timed
+ * region.  No counterpart in the paper: a measurement aid. */
+unsigned long long bch_kernel_launches(void);
 /* Library version string. */
 const char *bch_version(void);
 

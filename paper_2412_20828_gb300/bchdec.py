@@ -29,6 +29,8 @@ EXPORTS = (
     "bch_osd_decode",
     "bch_compact_failed", "bch_count_errors", "bch_nms_forward_train", "bch_nms_backward", "bch_bce_loss",
     "bch_train_alpha", "bch_decoder_create", "bch_decoder_run_host", "bch_decoder_destroy",
+    "bch_decoder_set_timing", "bch_decoder_get_timing", "bch_decoder_set_in_place",
+    "bch_kernel_launches",
     "bch_server_create", "bch_server_submit", "bch_server_poll", "bch_server_fetch",
     "bch_server_get_stats", "bch_server_kernel_info", "bch_serve_jit_check", "bch_server_destroy",
     "bch_serve_bench",
@@ -82,7 +84,7 @@ class ServeBenchResult(C.Structure):
 class NmsParams(C.Structure):
     _fields_ = [("iters", C.c_int), ("alpha", C.POINTER(C.c_float)), ("n_autos", C.c_int),
                 ("early_stop", C.c_int), ("msg", C.c_int), ("rescale", C.c_int),
-                ("osd_order", C.c_int)]
+                ("osd_order", C.c_int), ("osd_input", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -130,6 +132,10 @@ def load():
             "bch_decoder_create": (st, [P, P, C.POINTER(NmsParams), i, i, C.POINTER(P)]),
             "bch_decoder_run_host": (st, [P, P, i, u64, u64, P, P, P]),
             "bch_decoder_destroy": (None, [P]),
+            "bch_decoder_set_timing": (st, [P, i]),
+            "bch_decoder_get_timing": (st, [P, C.POINTER(DecoderTiming)]),
+            "bch_decoder_set_in_place": (st, [P, i]),
+            "bch_kernel_launches": (C.c_ulonglong, []),
             "bch_server_create": (st, [C.POINTER(ServerConfig), C.POINTER(P)]),
             "bch_server_submit": (st, [P, i, P, i, i, u64, u64, C.POINTER(u64)]),
             "bch_server_poll": (st, [P, P, i, C.POINTER(i), i]),
@@ -268,11 +274,15 @@ def serve_jit_check(codes, seed=0x2412_20828) -> str:
     return buf.value.decode(errors="replace")
 
 
-def params(iters, alpha, n_autos=3, early_stop=True, msg=MSG_FP32, rescale=False, osd_order=2):
+OSD_CHANNEL, OSD_NMS_OUTPUT = 0, 1
+
+
+def params(iters, alpha, n_autos=3, early_stop=True, msg=MSG_FP32, rescale=False, osd_order=2,
+           osd_input=OSD_CHANNEL):
     """Builds a bch_nms_params; ``alpha`` is a scalar or one factor per iteration."""
     al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float32), (iters,)))
     p = NmsParams(iters, al.ctypes.data_as(C.POINTER(C.c_float)), n_autos, int(early_stop), msg,
-                  int(rescale), osd_order)
+                  int(rescale), osd_order, int(osd_input))
     p._alpha_keepalive = al  # the C struct points into this array
     return p
 
@@ -407,6 +417,17 @@ def train_alpha(code: Code, n_autos, iters, alpha, steps, batch, ebn0_lo, ebn0_h
     return al, hist[:steps]
 
 
+class DecoderTiming(C.Structure):
+    _fields_ = [("calls", C.c_longlong), ("chunks", C.c_longlong), ("in_place_chunks", C.c_longlong),
+                ("ms_wall", C.c_double),
+                ("ms_h2d", C.c_double), ("ms_decode", C.c_double), ("ms_d2h", C.c_double)]
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process (bch_kernel_launches)."""
+    return int(load().bch_kernel_launches())
+
+
 class HostDecoder:
     """bch_decoder: decodes frames held in host memory with overlapped transfers."""
 
@@ -424,6 +445,19 @@ class HostDecoder:
         F = llr.shape[0]
         _check(load().bch_decoder_run_host(self._h, _ptr(llr), F, autos_seed, frame0, _ptr(hard),
                                            _ptr(iters), _ptr(flags)), "bch_decoder_run_host")
+
+    def set_in_place(self, on=True):
+        """Decode mapped page-locked host buffers in place (default) or stage copies."""
+        _check(load().bch_decoder_set_in_place(self._h, int(on)), "bch_decoder_set_in_place")
+
+    def set_timing(self, on=True):
+        """Per-phase timing of the later run() calls (bch_decoder_set_timing)."""
+        _check(load().bch_decoder_set_timing(self._h, int(on)), "bch_decoder_set_timing")
+
+    def timing(self) -> dict:
+        t = DecoderTiming()
+        _check(load().bch_decoder_get_timing(self._h, C.byref(t)), "bch_decoder_get_timing")
+        return {f: getattr(t, f) for f, _ in DecoderTiming._fields_}
 
     def close(self):
         if self._h:

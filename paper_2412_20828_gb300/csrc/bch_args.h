@@ -20,6 +20,7 @@ struct OsdArgs {
   uint64_t *hard;
   uint8_t *flags;
   unsigned *queue;
+  int scale_input;  // 1: scale each frame's input by the power of two putting max |L| in [2^15, 2^16)
 };
 
 struct GenArgs {

@@ -93,6 +93,8 @@ struct bch_code {
 namespace bchlib {
 void set_error(const std::string &msg);
 bch_status fail(bch_status s, const std::string &msg);
+// Counts one kernel launch of the library (bch_kernel_launches reports the total).
+void note_launch();
 // Argument checks shared by the decode entry points (BCH_EINVAL with a message).
 bch_status check_params(const bch_code *code, const bch_nms_params *p);
 bch_status check_frames(const bch_code *code, const float *llr, int ld, int F);

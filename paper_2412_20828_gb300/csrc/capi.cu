@@ -1,6 +1,7 @@
 // C ABI of the decoder library: argument checking, code objects, workspace layout and
 // the launch sequences of the decode / training calls.  See include/bchdec.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -42,6 +43,9 @@ static int kernel_mode() {
 namespace bchlib {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -162,6 +166,7 @@ bch_status check_params(const bch_code *code, const bch_nms_params *p) {
     return fail(BCH_EINVAL, "the plain decoder supports FP32 only");
   for (int t = 0; t < p->iters; t++)
     if (!std::isfinite(p->alpha[t])) return fail(BCH_EINVAL, "alpha must be finite");
+  if (p->osd_input != 0 && p->osd_input != 1) return fail(BCH_EINVAL, "osd_input must be 0 or 1");
   return BCH_OK;
 }
 
@@ -327,6 +332,8 @@ const char *bch_status_str(bch_status s) {
 const char *bch_last_error(void) { return g_last_error.c_str(); }
 
 const char *bch_version(void) { return "bchdec-gb300 1.0 (sm_103a)"; }
+
+unsigned long long bch_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 static bch_status build_host(int n, int k, bch_pcm_kind kind, int m_rows, uint64_t seed,
                              const bch_pcm_opts *opts, bch_code *c) {
@@ -536,6 +543,7 @@ static cudaError_t launch_jit(cudaKernel_t k, const bch_code *code, const NmsArg
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   void *args[] = {const_cast<NmsArgs *>(&a)};
+  note_launch();
   return cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(unsigned(tpb)), args, smem, st);
 }
 
@@ -588,7 +596,7 @@ bch_status bch_nms_decode(const bch_code *code, const bch_nms_params *params, co
 
 static bch_status run_osd(const bch_code *std_code, int order, const float *llr, int ld,
                           const uint32_t *list, const uint32_t *count, int max_frames, uint64_t *hard,
-                          uint8_t *flags, unsigned *queue, cudaStream_t st) {
+                          uint8_t *flags, unsigned *queue, cudaStream_t st, int scale_input = 0) {
   bch_status s = check_osd(nullptr, std_code, order);
   if (s != BCH_OK) return s;
   const int n = std_code->alg.n, M = n - std_code->alg.k;
@@ -608,6 +616,7 @@ static bch_status run_osd(const bch_code *std_code, int order, const float *llr,
   a.hard = hard;
   a.flags = flags;
   a.queue = queue;
+  a.scale_input = scale_input;
   BCH_CUDA(launch_osd(a, st), "osd kernel");
   return BCH_OK;
 }
@@ -635,6 +644,8 @@ bch_status bch_hybrid_decode(const bch_code *code, const bch_code *std_code, con
   bch_status s = check_params(code, params);
   if (s == BCH_OK) s = check_osd(code, std_code, params->osd_order);
   if (s != BCH_OK) return s;
+  if (params->osd_input == 1 && !llr_out)
+    return fail(BCH_EINVAL, "osd_input = 1 needs llr_out (the NMS output the OSD reads)");
   s = run_nms(code, params, llr, ld, n_frames, autos, hard, iters, flags, llr_out, nullptr,
                          workspace, st);
   if (s != BCH_OK || n_frames == 0) return s;
@@ -645,6 +656,9 @@ bch_status bch_hybrid_decode(const bch_code *code, const bch_code *std_code, con
   BCH_CUDA(launch_compact(flags, n_frames, reinterpret_cast<uint32_t *>(ws + L.counts), list, count, st),
            "compaction");
   unsigned *queue = reinterpret_cast<unsigned *>(ws + L.queues);
+  if (params->osd_input == 1)  // the failed frames' final y, scaled per frame in the OSD
+    return run_osd(std_code, params->osd_order, llr_out, ld, list, count, n_frames, hard, flags, queue + 1,
+                   st, 1);
   return run_osd(std_code, params->osd_order, llr, ld, list, count, n_frames, hard, flags, queue + 1, st);
 }
 

@@ -93,13 +93,12 @@ const char *row_macros(int msg) {
   if (msg == 2)
     return R"(
 #define BCH_VT int
-#define BCH_R0 { int m1_ = 1 << 20, m2_ = 1 << 20, a_;
-#define BCH_R1(u) a_ = abs(z[u]); m2_ = min(m2_, max(m1_, a_)); m1_ = min(m1_, a_);
+#define BCH_R0 { int m1_ = 1 << 20, m2_ = 1 << 20;
+#define BCH_R1(u) { const int a_ = abs(z[u]); m2_ = min(m2_, max(m1_, a_)); m1_ = min(m1_, a_); }
 #define BCH_R1F(u, v) { const int p_ = abs(z[u]), q_ = abs(z[v]); m1_ = min(p_, q_); m2_ = max(p_, q_); }
 #define BCH_R1P(u, v) { const int p_ = abs(z[u]), q_ = abs(z[v]); const int lo_ = min(p_, q_); \
   m2_ = __vimin3_s32(m2_, max(m1_, lo_), max(p_, q_)); m1_ = min(m1_, lo_); }
-#define BCH_RM(SG) const int c1_ = __double2int_rn(double(alpha) * double(m1_)); \
-  const int c2_ = __double2int_rn(double(alpha) * double(m2_)); \
+#define BCH_RM(SG) const int c1_ = rne_product(alpha, m1_); const int c2_ = rne_product(alpha, m2_); \
   const bool neg_ = (SG); const int v1_ = neg_ ? -c1_ : c1_; const int dv_ = (neg_ ? -c2_ : c2_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) BCH_R2(u)
@@ -116,8 +115,8 @@ const char *row_macros(int msg) {
 #define BCH_R1P(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); const float lo_ = fminf(a_, b_); \
   m2_ = bch_min3f(m2_, fmaxf(m1_, lo_), fmaxf(a_, b_)); m1_ = fminf(m1_, lo_); }
 #define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
-  const float v1_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m1_))), sg_); \
-  const float dv_ = flip_sign(__half2float(half_sat_d(double(alpha) * double(m2_))), sg_) - v1_;
+  const float v1_ = flip_sign(half_product(alpha, m1_), sg_); \
+  const float dv_ = flip_sign(half_product(alpha, m2_), sg_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) { const float p_ = (fabsf(z[u]) - m1_) * 0x1p100f; \
   BCH_SV(u) = __fmaf_rn(dv_, __saturatef(__fmaf_rn(-p_, 0x1p100f, 1.0f)), BCH_SV(u) + v1_); }

@@ -18,6 +18,7 @@ __global__ void draw_autos_kernel(int n, int ord, int P, uint64_t seed, uint64_t
 cudaError_t launch_draw_autos(int n, int ord, int P, uint64_t seed, uint64_t frame0, int F,
                               uint16_t *out, cudaStream_t st) {
   if (F <= 0) return cudaSuccess;
+  note_launch();
   draw_autos_kernel<<<(F + 255) / 256, 256, 0, st>>>(n, ord, P, seed, frame0, F, out);
   return cudaGetLastError();
 }
@@ -100,6 +101,7 @@ __global__ void gen_frames_kernel(const GenArgs a) {
 
 cudaError_t launch_gen_frames(const GenArgs &a, cudaStream_t st) {
   if (a.F <= 0) return cudaSuccess;
+  note_launch();
   gen_frames_kernel<<<(a.F + 127) / 128, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
@@ -141,6 +143,7 @@ __global__ void count_errors_kernel(int n, const uint64_t *hard, const uint64_t 
 cudaError_t launch_count_errors(int n, const uint64_t *hard, const uint64_t *cw, const uint8_t *iters,
                                 const uint8_t *flags, int F, long long *counters, cudaStream_t st) {
   if (F <= 0) return cudaSuccess;
+  note_launch();
   count_errors_kernel<<<(F + 255) / 256, 256, 0, st>>>(n, hard, cw, iters, flags, F, counters);
   return cudaGetLastError();
 }
@@ -195,7 +198,9 @@ cudaError_t launch_bce(int n, const float *y, int ld, const uint64_t *cw, int F,
                        float *grad, float *partial, cudaStream_t st) {
   if (F <= 0) return cudaMemsetAsync(loss, 0, sizeof(float), st);
   const int nb = (F + 255) / 256;
+  note_launch();
   bce_kernel<<<nb, 256, 0, st>>>(n, y, ld, cw, F, grad, partial);
+  note_launch();
   sum_partials_kernel<<<1, 256, 0, st>>>(partial, nb, 1.0f / (float(F) * float(n)), loss);
   return cudaGetLastError();
 }

@@ -175,6 +175,7 @@ static cudaError_t launch_persistent(K kernel, int tpb, size_t smem, const NmsAr
   const long long need = (a.F + tpb - 1) / tpb;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
+  note_launch();
   kernel<<<unsigned(blocks), tpb, smem, st>>>(a);
   return cudaGetLastError();
 }

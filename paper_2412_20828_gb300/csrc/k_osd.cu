@@ -33,8 +33,10 @@ __global__ void __launch_bounds__(32 * kOsdWarps) osd_kernel(const OsdArgs a) {
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
     const int f = int(a.list[item]);
-    osd_one_frame(S, a.n, a.k, a.M, a.cols, a.llr + size_t(f) * a.ld, a.order, a.hard + size_t(f) * W64,
-                  a.flags ? a.flags + f : nullptr);
+    const float *L = a.llr + size_t(f) * a.ld;
+    const int sexp = a.scale_input ? osd_input_exponent(L, a.n) : 0;
+    osd_one_frame(S, a.n, a.k, a.M, a.cols, L, a.order, a.hard + size_t(f) * W64,
+                  a.flags ? a.flags + f : nullptr, sexp);
   }
 }
 
@@ -92,7 +94,9 @@ cudaError_t launch_compact(const uint8_t *flags, int F, uint32_t *counts, uint32
                            uint32_t *count, cudaStream_t st) {
   if (F <= 0) return cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
   const int nb = (F + kCompactBlock - 1) / kCompactBlock;
+  note_launch();
   count_failed_kernel<<<nb, kCompactBlock, 0, st>>>(flags, F, counts);
+  note_launch();
   write_failed_kernel<<<nb, kCompactBlock, 0, st>>>(flags, F, counts, list, count);
   return cudaGetLastError();
 }
@@ -106,6 +110,7 @@ cudaError_t launch_osd(const OsdArgs &a, cudaStream_t st) {
   const long long need = (a.max_frames + kOsdWarps - 1) / kOsdWarps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
+  note_launch();
   osd_kernel<<<unsigned(blocks), 32 * kOsdWarps, smem, st>>>(a);
   return cudaGetLastError();
 }

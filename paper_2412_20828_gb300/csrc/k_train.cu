@@ -197,6 +197,7 @@ static cudaError_t launch_bwd_wb(const BwdArgs &a, int nb, size_t smem, cudaStre
   cudaError_t e = cudaFuncSetAttribute(nms_backward_kernel<TPB, WB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
+  note_launch();
   nms_backward_kernel<TPB, WB><<<nb, TPB, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -227,6 +228,7 @@ cudaError_t launch_backward(const BwdArgs &a0, float *grad_alpha, cudaStream_t s
   else
     e = cudaErrorNotSupported;
   if (e != cudaSuccess) return e;
+  note_launch();
   reduce_alpha_kernel<<<a0.I, 256, 0, st>>>(a0.partial, nb, a0.I, grad_alpha);
   return cudaGetLastError();
 }

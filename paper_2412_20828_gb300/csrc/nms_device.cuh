@@ -83,10 +83,6 @@ __device__ __forceinline__ __half to_half_sat(float x) {
   x = fminf(fmaxf(x, -65504.0f), 65504.0f);
   return half_pz(__float2half_rn(x));
 }
-__device__ __forceinline__ __half half_sat_d(double x) {
-  x = fmin(fmax(x, -65504.0), 65504.0);
-  return __double2half(x);
-}
 // FP16 merge: the binary16 value nearest to num / P (num = P y + sum of c2v), ties
 // to even, saturating at +-65504, with num exact.  The FP32 quotient q = fl(num / P)
 // lies on the same side of every binary16 rounding point as the exact quotient (RN is
@@ -105,6 +101,34 @@ __device__ __forceinline__ __half half_of_quotient(float num, float P) {
     if (d < 0.0f) h = lo;
   }
   return half_pz(h);
+}
+
+// Check-to-variable magnitudes of the reduced formats, rounded once from the exact
+// product alpha * m without FP64 arithmetic (which runs at a small fraction of the FP32
+// rate): hi = fl(alpha m) and lo = fma(alpha, m, -hi) = alpha m - hi exactly (the
+// error-free product).  hi lies on the same side of every rounding point as the exact
+// product (RN is monotone and those points are FP32 values), so rounding hi is right
+// unless hi landed exactly on a rounding point; then lo says which side the exact
+// product is on.
+// INT8: rne(alpha m) for an integer m, as an int.
+__device__ __forceinline__ int rne_product(float alpha, int m) {
+  const float b = float(m);
+  const float hi = alpha * b, lo = __fmaf_rn(alpha, b, -hi);
+  const float fl = floorf(hi);
+  float r = rintf(hi);
+  if (hi - fl == 0.5f) r = lo > 0.0f ? fl + 1.0f : (lo < 0.0f ? fl : r);
+  return int(r);
+}
+// FP16: the binary16 value nearest to alpha m (ties to even, saturating at +-65504),
+// returned as a float.
+__device__ __forceinline__ float half_product(float alpha, float m) {
+  const float hi = alpha * m, lo = __fmaf_rn(alpha, m, -hi);
+  if (fabsf(hi) >= 65504.0f) return copysignf(65504.0f, hi);
+  const __half dn = __float2half_rd(hi), up = __float2half_ru(hi);
+  const float fdn = __half2float(dn), fup = __half2float(up);
+  float r = __half2float(__float2half_rn(hi));
+  if (fdn != fup && hi == 0.5f * (fdn + fup)) r = lo > 0.0f ? fup : (lo < 0.0f ? fdn : r);
+  return r;
 }
 
 // INT8 store: rne, saturating at +-31 (LSB = 1/4 of an LLR unit).
@@ -163,9 +187,9 @@ __device__ __forceinline__ void enh_rows(const uint16_t *__restrict__ codes, int
           }
         }
       }
-      // c2v magnitudes are integers: rne(alpha * min), the product formed exactly
-      const int c1 = __double2int_rn(double(alpha) * double(m1));
-      const int c2 = __double2int_rn(double(alpha) * double(m2));
+      // c2v magnitudes are integers: rne(alpha * min) of the exact product
+      const int c1 = rne_product(alpha, m1);
+      const int c2 = rne_product(alpha, m2);
       const int s1 = (sg & kSign) ? -c1 : c1;
       const int s2 = (sg & kSign) ? -c2 : c2;
       A o[WB];
@@ -208,10 +232,10 @@ __device__ __forceinline__ void enh_rows(const uint16_t *__restrict__ codes, int
       }
       float v1, v2;
       if constexpr (MSG == kFP16) {
-        // messages are stored in binary16: alpha * min is formed exactly (a float
-        // times a binary16 value fits a double) and rounded once
-        v1 = flip_sign(__half2float(half_sat_d(double(alpha) * double(m1))), sg);
-        v2 = flip_sign(__half2float(half_sat_d(double(alpha) * double(m2))), sg);
+        // messages are stored in binary16: alpha * min rounded once from the exact
+        // product
+        v1 = flip_sign(half_product(alpha, m1), sg);
+        v2 = flip_sign(half_product(alpha, m2), sg);
       } else {
         v1 = flip_sign(alpha * m1, sg);
         v2 = flip_sign(alpha * m2, sg);

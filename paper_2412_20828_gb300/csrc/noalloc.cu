@@ -103,6 +103,8 @@ extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_
   if (n_frames == 0) return BCH_OK;
   if (!hard || !flags) return fail(BCH_EINVAL, "hybrid decoding needs hard and flags");
   if (p->n_autos > 0 && !autos) return fail(BCH_EINVAL, "autos is null");
+  if (p->osd_input == 1 && !llr_out)
+    return fail(BCH_EINVAL, "osd_input = 1 needs llr_out (the NMS output the OSD reads)");
   void *base = nullptr;
   s = scratch_address(&base);
   if (s != BCH_OK) return s;
@@ -147,8 +149,9 @@ extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_
   o.M = M;
   o.rows = reinterpret_cast<const uint4 *>(std_code->dc.rowmask);
   o.cols = std_code->dc.colmask;
-  o.llr = llr;
+  o.llr = p->osd_input == 1 ? llr_out : llr;
   o.ld = ld;
+  o.scale_input = p->osd_input == 1 ? 1 : 0;
   o.list = list;
   o.count = count;
   o.max_frames = n_frames;

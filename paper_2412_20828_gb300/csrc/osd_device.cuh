@@ -96,7 +96,7 @@ __device__ __forceinline__ int ffs_mask(MT v) {
 template <typename MT>
 __device__ __forceinline__ void osd_one_frame_t(OsdSmem &S, int n, int K, int M, const uint64_t *cols,
                                                 const float *L, int order, uint64_t *hard,
-                                                uint8_t *flag) {
+                                                uint8_t *flag, int sexp) {
   const int lane = int(lane_id());
   // ---- reliabilities, hard decision, sort keys
   uint4 h = make_uint4(0, 0, 0, 0);
@@ -104,7 +104,7 @@ __device__ __forceinline__ void osd_one_frame_t(OsdSmem &S, int n, int K, int M,
 #pragma unroll
   for (int r = 0; r < 4; r++) {
     const int i = lane + 32 * r;
-    const float lv = i < n ? L[i] : 0.0f;
+    const float lv = i < n ? ldexpf(L[i], sexp) : 0.0f;
     const float al = fabsf(lv);
     const unsigned hb = __ballot_sync(kFull, i < n && lv < 0.0f);
     if (r == 0) h.x = hb;
@@ -182,12 +182,12 @@ __device__ __forceinline__ void osd_one_frame_t(OsdSmem &S, int n, int K, int M,
   // weights by original index are held per lane (wv); gather the needed ones
   for (int a2 = lane; a2 < K; a2 += 32) {
     const int ci = S.mrb[a2];
-    const float al = fabsf(L[ci]);
+    const float al = fabsf(ldexpf(L[ci], sexp));
     S.wm[a2] = __float2ull_rz(fminf(floorf(al * 16777216.0f), 1099511627776.0f));
   }
   // weights of the pivot positions, by row
   for (int r = lane; r < 64; r += 32) {
-    const float al = r < M ? fabsf(L[S.pivcol[r]]) : 0.f;
+    const float al = r < M ? fabsf(ldexpf(L[S.pivcol[r]], sexp)) : 0.f;
     S.wp[r] = r < M ? __float2ull_rz(fminf(floorf(al * 16777216.0f), 1099511627776.0f)) : 0ull;
   }
   // basis columns restricted to the pivot rows
@@ -295,13 +295,26 @@ __device__ __forceinline__ void osd_one_frame_t(OsdSmem &S, int n, int K, int M,
   __syncwarp();
 }
 
-// Dispatch on the row count: 32-bit row masks when M <= 32.
+// Dispatch on the row count: 32-bit row masks when M <= 32.  The frame's input values
+// are L[i] 2^sexp (ldexpf: exact while the result stays in the normal range).
 __device__ __forceinline__ void osd_one_frame(OsdSmem &S, int n, int K, int M, const uint64_t *cols,
-                                              const float *L, int order, uint64_t *hard, uint8_t *flag) {
+                                              const float *L, int order, uint64_t *hard, uint8_t *flag,
+                                              int sexp = 0) {
   if (M <= 32)
-    osd_one_frame_t<uint32_t>(S, n, K, M, cols, L, order, hard, flag);
+    osd_one_frame_t<uint32_t>(S, n, K, M, cols, L, order, hard, flag, sexp);
   else
-    osd_one_frame_t<unsigned long long>(S, n, K, M, cols, L, order, hard, flag);
+    osd_one_frame_t<unsigned long long>(S, n, K, M, cols, L, order, hard, flag, sexp);
+}
+
+// Exponent e that puts max_i |L_i| 2^e in [2^15, 2^16) (e = 16 - frexp exponent of the
+// maximum; 16 when every value is zero), computed by the whole warp.
+__device__ __forceinline__ int osd_input_exponent(const float *L, int n) {
+  float mx = 0.0f;
+  for (int i = int(lane_id()); i < n; i += 32) mx = fmaxf(mx, fabsf(L[i]));
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, off));
+  int ex = 0;
+  frexpf(mx, &ex);
+  return 16 - ex;
 }
 
 }  // namespace bchlib

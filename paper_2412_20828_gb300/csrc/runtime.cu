@@ -5,6 +5,7 @@
 // about 210 GB/s each way; chunks of ~1M frames keep the copies hidden behind the
 // decode while keeping few decode launches (each ends in a tail where the slowest
 // frames of the last wave finish on a partly idle GPU).
+#include <chrono>
 #include <cstring>
 #include <new>
 #include <string>
@@ -27,11 +28,33 @@ struct bch_decoder {
     uint64_t *hard = nullptr;
     uint8_t *iters = nullptr;
     uint8_t *flags = nullptr;
+    float *y = nullptr;  // final NMS output, when the OSD reads it (osd_input = 1)
     void *ws = nullptr;
   } slot[2];
+  bool timing = false;
+  bool in_place = true;  // decode device-accessible host buffers where they are
+  bch_decoder_timing tm{};
 };
 
 namespace {
+// Device address of [p, p + count) when the GPU can read and write that host memory in
+// place -- page-locked memory mapped into the device's address space (under unified
+// addressing at the same address) -- else nullptr.  Both ends are checked, so a range
+// that leaves its mapped allocation is not taken.
+template <class T>
+T *device_view(T *p, size_t count) {
+  if (!p || count == 0) return nullptr;
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, p + (count - 1)) != cudaSuccess) {
+    cudaGetLastError();  // clear a non-sticky error of the query
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+    return nullptr;
+  T *da = static_cast<T *>(a.devicePointer), *db = static_cast<T *>(b.devicePointer);
+  return db - da == std::ptrdiff_t(count - 1) ? da : nullptr;
+}
+
 void free_decoder(bch_decoder *d) {
   for (int b = 0; b < 2; b++) {
     cudaFree(d->slot[b].llr);
@@ -39,6 +62,7 @@ void free_decoder(bch_decoder *d) {
     cudaFree(d->slot[b].hard);
     cudaFree(d->slot[b].iters);
     cudaFree(d->slot[b].flags);
+    cudaFree(d->slot[b].y);
     cudaFree(d->slot[b].ws);
     if (d->st[b]) cudaStreamDestroy(d->st[b]);
   }
@@ -80,7 +104,8 @@ bch_status bch_decoder_create(const bch_code *code, const bch_code *std_code,
               cudaMalloc(&S.autos, F * P * 2) == cudaSuccess &&
               cudaMalloc(&S.hard, F * d->W64 * 8) == cudaSuccess &&
               cudaMalloc(&S.iters, F) == cudaSuccess && cudaMalloc(&S.flags, F) == cudaSuccess &&
-              cudaMalloc(&S.ws, wsb) == cudaSuccess;
+              cudaMalloc(&S.ws, wsb) == cudaSuccess &&
+              (params->osd_input != 1 || cudaMalloc(&S.y, F * ld * 4) == cudaSuccess);
     if (!ok) {
       free_decoder(d);
       return fail(BCH_ENOMEM, "decoder buffers");
@@ -96,35 +121,106 @@ bch_status bch_decoder_run_host(bch_decoder *d, const float *llr, int n_frames, 
   if (n_frames < 0 || (n_frames > 0 && (!llr || !hard))) return fail(BCH_EINVAL, "bad arguments");
   const int n = d->code->alg.n;
   const int nchunks = (n_frames + d->chunk - 1) / d->chunk;
+  const auto t_wall = std::chrono::steady_clock::now();
+  // per-phase timing: events before the copy-in, after it, after the decode and after
+  // the copy-out of every chunk, read once the call's work has finished
+  struct Events {  // destroyed on every return path
+    std::vector<cudaEvent_t> v;
+    ~Events() {
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+  } evs;
+  std::vector<cudaEvent_t> &ev = evs.v;
+  auto mark = [&](cudaStream_t st) {
+    if (!d->timing) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) == cudaSuccess) {
+      cudaEventRecord(e, st);
+      ev.push_back(e);
+    }
+  };
+  // In place: when the caller's buffers are page-locked host memory mapped into the
+  // device's address space, the kernels read the LLRs and write the results there
+  // directly (on a GB300 over the coherent CPU-GPU link), with no staging copies; the
+  // chunks then only bound the automorphism and workspace buffers.  Otherwise each chunk
+  // is copied in and its results copied out.
+  const size_t Fz = size_t(n_frames);
+  const float *llr_d = d->in_place ? device_view(llr, Fz * d->ld) : nullptr;
+  uint64_t *hard_d = llr_d ? device_view(hard, Fz * d->W64) : nullptr;
+  uint8_t *iters_d = hard_d && iters ? device_view(iters, Fz) : nullptr;
+  uint8_t *flags_d = hard_d && flags ? device_view(flags, Fz) : nullptr;
+  const bool zc = llr_d && hard_d && (!iters || iters_d) && (!flags || flags_d);
   for (int c = 0; c < nchunks; c++) {
     const int b = c & 1;
     auto &S = d->slot[b];
     cudaStream_t st = d->st[b];
     const int f0 = c * d->chunk;
     const int F = std::min(d->chunk, n_frames - f0);
-    cudaError_t e = cudaMemcpyAsync(S.llr, llr + size_t(f0) * d->ld, size_t(F) * d->ld * 4,
-                                    cudaMemcpyHostToDevice, st);
+    mark(st);
+    cudaError_t e = cudaSuccess;
+    if (!zc)
+      e = cudaMemcpyAsync(S.llr, llr + size_t(f0) * d->ld, size_t(F) * d->ld * 4, cudaMemcpyHostToDevice, st);
+    mark(st);
     if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("copy in: ") + cudaGetErrorString(e));
+    const float *cl = zc ? llr_d + size_t(f0) * d->ld : S.llr;
+    uint64_t *ch = zc ? hard_d + size_t(f0) * d->W64 : S.hard;
+    uint8_t *ci = zc && iters_d ? iters_d + f0 : S.iters;
+    uint8_t *cf = zc && flags_d ? flags_d + f0 : S.flags;
     bch_status s = BCH_OK;
     if (d->params.n_autos > 0)
       s = bch_draw_automorphisms(n, d->params.n_autos, autos_seed, frame0 + uint64_t(f0), F, S.autos, st);
     if (s != BCH_OK) return s;
     if (d->std_code)
-      s = bch_hybrid_decode(d->code, d->std_code, &d->params, S.llr, d->ld, F, S.autos, S.hard, S.iters,
-                            S.flags, nullptr, nullptr, nullptr, S.ws, st);
+      s = bch_hybrid_decode(d->code, d->std_code, &d->params, cl, d->ld, F, S.autos, ch, ci, cf, S.y, nullptr,
+                            nullptr, S.ws, st);
     else
-      s = bch_nms_decode(d->code, &d->params, S.llr, d->ld, F, S.autos, S.hard, S.iters, S.flags, nullptr,
-                         S.ws, st);
+      s = bch_nms_decode(d->code, &d->params, cl, d->ld, F, S.autos, ch, ci, cf, nullptr, S.ws, st);
     if (s != BCH_OK) return s;
-    e = cudaMemcpyAsync(hard + size_t(f0) * d->W64, S.hard, size_t(F) * d->W64 * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && iters) e = cudaMemcpyAsync(iters + f0, S.iters, F, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags + f0, S.flags, F, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("copy out: ") + cudaGetErrorString(e));
+    mark(st);
+    if (!zc) {
+      e = cudaMemcpyAsync(hard + size_t(f0) * d->W64, S.hard, size_t(F) * d->W64 * 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess && iters) e = cudaMemcpyAsync(iters + f0, S.iters, F, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags + f0, S.flags, F, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("copy out: ") + cudaGetErrorString(e));
+    }
+    mark(st);
   }
   for (int b = 0; b < 2; b++) {
     cudaError_t e = cudaStreamSynchronize(d->st[b]);
     if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("decoder: ") + cudaGetErrorString(e));
   }
+  if (d->timing) {
+    d->tm.calls++;
+    d->tm.chunks += nchunks;
+    if (zc) d->tm.in_place_chunks += nchunks;
+    d->tm.ms_wall +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_wall).count();
+    double *acc[3] = {&d->tm.ms_h2d, &d->tm.ms_decode, &d->tm.ms_d2h};
+    for (size_t c = 0; c + 4 <= ev.size(); c += 4)
+      for (int q = 0; q < 3; q++) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ev[c + q], ev[c + q + 1]) == cudaSuccess) *acc[q] += ms;
+      }
+  }
+  return BCH_OK;
+}
+
+bch_status bch_decoder_set_timing(bch_decoder *d, int on) {
+  if (!d) return fail(BCH_EINVAL, "null decoder");
+  d->timing = on != 0;
+  d->tm = bch_decoder_timing{};
+  return BCH_OK;
+}
+
+bch_status bch_decoder_set_in_place(bch_decoder *d, int on) {
+  if (!d) return fail(BCH_EINVAL, "null decoder");
+  d->in_place = on != 0;
+  return BCH_OK;
+}
+
+bch_status bch_decoder_get_timing(const bch_decoder *d, bch_decoder_timing *out) {
+  if (!d || !out) return fail(BCH_EINVAL, "null argument");
+  *out = d->tm;
   return BCH_OK;
 }
 

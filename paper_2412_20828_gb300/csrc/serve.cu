@@ -232,6 +232,7 @@ bch_status launch_server_kernel(bch_server *s) {
   cudaError_t e = cudaMemsetAsync(&s->dv->live, 0, sizeof(unsigned), s->kst);
   if (e == cudaSuccess) {
     void *args[] = {&s->args};
+    note_launch();
     e = cudaLaunchKernel(s->kfn, dim3(unsigned(s->blocks)), dim3(32u), args, s->smem, s->kst);
   }
   if (e != cudaSuccess) {

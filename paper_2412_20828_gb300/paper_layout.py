@@ -1,12 +1,13 @@
 """The paper's own enhanced-NMS layout on the GPU decoder, for comparison with its
-printed error rates (Sec. III-B, Sec. IV, Fig. 2).
+printed error rates (Sec. III-B, Sec. IV, Fig. 2 to Fig. 4).
 
 Layout: P = 9 automorphisms per frame -- three cyclic shifts spaced d_p apart, each
 applied to y, to the interleaved word (z[u] = y[2u mod n]) and to the Frobenius word
 (z[u] = y[2^-1 u mod n]), with one random offset per frame; I_m = 4 iterations for
-n = 63; the Table I matrix sizes (BCH(63,36): 122 rows, BCH(63,45): 33 rows); one
-normalization factor, chosen by a sweep at 2.6 dB (the paper tunes its factor there
-for n = 63 and does not print it).
+n = 63 and 8 for n = 127; the Table I matrix sizes (BCH(63,36): 122 rows, BCH(63,45):
+33, BCH(127,64): 72, BCH(127,78): 57, BCH(127,99): 33); one normalization factor,
+chosen by a sweep at 2.6 dB for n = 63 and 3.0 dB for n = 127 (where the paper tunes
+its factors, which it does not print).
 
 In the library's map pi(i) = 2^j i + s with z[pi(i)] = y[i], the interleaved word is
 j = m - 1 (pi^-1(u) = 2u) and the Frobenius word is j = 1.
@@ -30,11 +31,19 @@ import sys
 
 import numpy as np
 
-# enhanced NMS(4) BER printed in Fig. 2 (Sec. IV): code -> (rows, {Eb/N0: BER})
+# enhanced NMS error rates printed in Fig. 2 (n = 63, 4 iterations, BER) and in
+# Fig. 3 / Fig. 4 (n = 127, 8 iterations; BER except the FER panel of BCH(127,99)),
+# Sec. IV, on the Table I matrix sizes: code -> (rows, measure, {Eb/N0: value})
 PRINTED = {
-    (63, 36): (122, {2.0: 0.03437, 3.0: 0.00909, 4.0: 0.00104}),
-    (63, 45): (33, {3.0: 0.00965, 4.0: 0.00116}),
+    (63, 36): (122, "ber", {2.0: 0.03437, 3.0: 0.00909, 4.0: 0.00104}),
+    (63, 45): (33, "ber", {3.0: 0.00965, 4.0: 0.00116}),
+    (127, 64): (72, "ber", {3.0: 0.03689, 4.0: 0.00596, 5.0: 0.00024}),
+    (127, 78): (57, "ber", {3.0: 0.02608, 4.0: 0.00417}),
+    (127, 99): (33, "fer", {3.0: 0.514, 4.0: 0.131429, 5.0: 0.01050667, 6.0: 0.000191}),
 }
+# iterations and the Eb/N0 at which the normalization factor is tuned (Sec. IV:
+# 4 iterations for n = 63 and 8 for n = 127; factors trained at 2.6 and 3.0 dB)
+LAYOUT = {63: (4, 2.6), 127: (8, 3.0)}
 
 
 # redundancy ladder of BCH(63,36), Sec. III-A: (beta, M_o, FER at 3.5 dB), I_m = 4
@@ -61,26 +70,30 @@ def paper_block(n: int, m: int, frames: int, frame0: int, seed: int) -> np.ndarr
 
 
 def run(frames=1_000_000, alphas=(0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95, 1.0), chunk=1 << 19,
-        seed=0x2412, log=sys.stderr):
+        seed=0x2412, codes=None, log=sys.stderr):
     import torch
     from . import bchdec as B
     B.load()
-    res = {"frames_per_point": frames, "iters": 4, "P": 9, "codes": {}}
-    for (n, k), (rows, printed) in PRINTED.items():
-        m = 6
+    res = {"frames_per_point": frames, "P": 9, "codes": {}}
+    for (n, k), (rows, measure, printed) in PRINTED.items():
+        if codes is not None and (n, k) not in codes:
+            continue
+        m = 6 if n == 63 else 7
+        iters, tune_db = LAYOUT[n]
         code = B.Code(n, k, m_rows=rows)
-        ld = 64
+        ld = 64 if n == 63 else 128
+        W64 = (n + 63) // 64
         Fc = min(chunk, frames)
         llr = torch.empty((Fc, ld), dtype=torch.float32, device="cuda")
-        cw = torch.empty((Fc, 1), dtype=torch.int64, device="cuda")
-        hard = torch.empty((Fc, 1), dtype=torch.int64, device="cuda")
+        cw = torch.empty((Fc, W64), dtype=torch.int64, device="cuda")
+        hard = torch.empty((Fc, W64), dtype=torch.int64, device="cuda")
         its = torch.empty(Fc, dtype=torch.uint8, device="cuda")
         flg = torch.empty(Fc, dtype=torch.uint8, device="cuda")
-        ws = B.workspace(code, B.params(4, 0.7, n_autos=9), Fc)
+        ws = B.workspace(code, B.params(iters, 0.7, n_autos=9), Fc)
 
         def decode(ebn0, alpha, total, base):
             ctr = torch.zeros(8, dtype=torch.int64, device="cuda")
-            p = B.params(4, alpha, n_autos=9)
+            p = B.params(iters, alpha, n_autos=9)
             for f0 in range(0, total, Fc):
                 F = min(Fc, total - f0)
                 B.gen_frames(code, ebn0, ebn0, seed, base + f0, llr[:F], cw[:F])
@@ -91,19 +104,21 @@ def run(frames=1_000_000, alphas=(0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95, 1.
             return {"frames": int(c[0]), "fer": float(c[1] / c[0]), "ber": float(c[2] / (c[0] * n)),
                     "bit_errors": int(c[2]), "frame_errors": int(c[1])}
 
-        sweep = {a: decode(2.6, a, min(frames, 200_000), 10**9) for a in alphas}
+        sweep = {a: decode(tune_db, a, min(frames, 200_000), 10**9) for a in alphas}
         best = min(alphas, key=lambda a: sweep[a]["fer"])
         pts = {}
-        for e, ber_p in printed.items():
+        for e, val_p in printed.items():
             r = decode(e, best, frames, int(e * 10) * 10**9 + 2 * 10**9)
-            r["paper_ber"] = ber_p
-            r["ratio"] = r["ber"] / ber_p
+            r["measure"] = measure
+            r["paper"] = val_p
+            r["ratio"] = r[measure] / val_p
             pts[str(e)] = r
-        res["codes"][f"({n},{k})"] = {"rows": code.rows, "edges": code.edges,
-                                      "alpha_sweep_2p6dB_fer": {str(a): sweep[a]["fer"] for a in alphas},
+        res["codes"][f"({n},{k})"] = {"rows": code.rows, "edges": code.edges, "iters": iters,
+                                      "alpha_tuned_at_db": tune_db,
+                                      "alpha_sweep_fer": {str(a): sweep[a]["fer"] for a in alphas},
                                       "alpha": best, "points": pts}
         print(f"({n},{k}) alpha={best} " + " ".join(
-            f"{e}dB ber={v['ber']:.3e} (paper {v['paper_ber']:.3e})" for e, v in pts.items()), file=log)
+            f"{e}dB {measure}={v[measure]:.3e} (paper {v['paper']:.3e})" for e, v in pts.items()), file=log)
         code.close()
     return res
 
@@ -185,8 +200,12 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=1_000_000)
     ap.add_argument("--json", default=None)
     ap.add_argument("--ladder", action="store_true", help="the BCH(63,36) redundancy ladder")
+    ap.add_argument("--codes", default=None, help="e.g. 127,78;127,64 (default: every printed code)")
     a = ap.parse_args(argv)
-    res = run_ladder(a.frames) if a.ladder else run(a.frames)
+    codes = None
+    if a.codes:
+        codes = [tuple(int(x) for x in c.split(",")) for c in a.codes.split(";")]
+    res = run_ladder(a.frames) if a.ladder else run(a.frames, codes=codes)
     print(json.dumps(res, indent=1))
     if a.json:
         with open(a.json, "w") as f:

@@ -11,7 +11,7 @@ from paper_2412_20828_gb300 import bchdec as B
 
 pytestmark = pytest.mark.gpu
 
-CODES = [(15, 7), (63, 36), (63, 45), (127, 64), (127, 99)]
+CODES = [(15, 7), (63, 36), (63, 45), (127, 64), (127, 78), (127, 99)]
 
 
 @pytest.fixture(scope="module")
@@ -209,7 +209,7 @@ def test_plain_nms_standard_h(torch_cuda, ebn0):
 
 
 # ------------------------------------------------------------------ OSD and hybrid
-@pytest.mark.parametrize("nk", [(15, 7), (63, 36), (63, 45), (127, 64), (127, 99)])
+@pytest.mark.parametrize("nk", CODES)
 def test_osd_order2_bit_exact(torch_cuda, nk):
     torch = torch_cuda
     n, k = nk
@@ -245,8 +245,8 @@ def test_osd_partial_list(torch_cuda):
     assert np.all(h[others] == -1)
 
 
-@pytest.mark.parametrize("nk,ebn0", [((127, 99), 3.0), ((127, 64), 2.5), ((63, 36), 2.0),
-                                     ((15, 7), 2.0)])
+@pytest.mark.parametrize("nk,ebn0", [((127, 99), 3.0), ((127, 78), 3.0), ((127, 64), 2.5),
+                                     ((63, 36), 2.0), ((15, 7), 2.0)])
 def test_hybrid_matches_oracle(torch_cuda, nk, ebn0):
     torch = torch_cuda
     n, k = nk
