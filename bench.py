@@ -393,6 +393,41 @@ def run_config4(B, torch, dev, clocks, frames_per_point, steps=2, warmup=1):
     return out
 
 
+def run_pcm_search(B, torch, dev, chains=1216, n=63, k=36, frames=1_000_000, ebn0=3.0):
+    """The device-side H_o search (Sec. III-A step 6 as parallel annealing chains, one
+    block per chain; 1216 = 8 blocks on each of 152 SMs): its time, the 4-cycles of the
+    kept matrix against chain 0 (the matrix bch_build_pcm builds) and the enhanced-NMS
+    FER of both on the same frames."""
+    t0 = time.perf_counter()
+    best_code, best, stats = B.search_pcm(n, k, chains)
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    base = B.Code(n, k)
+    dt_host = time.perf_counter() - t1
+    out = {"workload": f"BCH({n},{k}) H_o with 2(n-k) rows, {chains} annealing chains of 20000 proposals",
+           "chains": chains, "search_s": dt, "host_build_s_one_chain": dt_host, "kept_chain": best,
+           "four_cycles": {"chain0": int(stats[0, 0]), "kept": int(stats[best, 0]),
+                           "median": float(np.median(stats[:, 0])), "min": int(stats[:, 0].min())}}
+    ld = 64
+    llr = torch.empty((frames, ld), dtype=torch.float32, device=dev)
+    cw = torch.empty((frames, 1), dtype=torch.int64, device=dev)
+    B.gen_frames(base, ebn0, ebn0, SEED_FRAMES + 9, 0, llr, cw)
+    aut = torch.empty((frames, P_AUTOS), dtype=torch.int16, device=dev)
+    B.draw_automorphisms(n, P_AUTOS, SEED_AUTOS + 9, 0, aut)
+    hard = torch.empty((frames, 1), dtype=torch.int64, device=dev)
+    p = B.params(ITERS, ALPHA, n_autos=P_AUTOS)
+    fer = {}
+    for name, c in (("chain0", base), ("kept", best_code)):
+        B.nms_decode(c, p, llr, aut, hard)
+        fe = int((hard != cw).any(dim=1).sum())
+        fer[name] = {"fer": fe / frames, "frame_errors": fe,
+                     "fer_ci95": list(clopper_pearson(fe, frames))}
+    out["nms_fer_at_%gdB" % ebn0] = fer
+    base.close()
+    best_code.close()
+    return out
+
+
 def run_training(B, torch, steps, batch=65536, iters=12):
     """BCH(127,64) enhanced NMS (P = 3), alpha_1..alpha_12 trained from 0.78 by Adam on
     batches of 65 536 frames at Eb/N0 uniform in [2, 5] dB that the library simulates,
@@ -433,6 +468,8 @@ def main():
                     help="Adam steps of the BCH(127,64) alpha_t training leg (0 skips it)")
     ap.add_argument("--config4-frames-per-point", type=int, default=1_000_000,
                     help="frames per point of the BCH(127,64)+BCH(127,99) hybrid leg (0 skips it)")
+    ap.add_argument("--search-chains", type=int, default=1216,
+                    help="annealing chains of the device-side H_o search leg (0 skips it)")
     ap.add_argument("--msg-legs", default="fp16,int8",
                     help="storage formats whose config-2 step is also timed ('' skips)")
     args = ap.parse_args()
@@ -674,6 +711,10 @@ def main():
             d.close()
 
     progress("end-to-end done")
+    pcm_search = None
+    if rank == 0 and args.search_chains > 0:
+        pcm_search = run_pcm_search(B, torch, dev, chains=args.search_chains)
+        progress("H_o search done")
     # ---- config 4: hybrid decoding of the two n = 127 codes, own roofline
     config4 = None
     if rank == 0 and args.config4_frames_per_point > 0:
@@ -766,7 +807,7 @@ def main():
             "edge_updates_per_s": eups, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": launches,
             "gpu_launches_basis": "library kernel launches counted (bch_kernel_launches) over the timed steps",
-            "msg_legs": msg_legs, "config4": config4,
+            "msg_legs": msg_legs, "config4": config4, "pcm_search": pcm_search,
             "serving": serving, "training": training, "plain_nms": plain,
             "fer_match_oracle_ci95": fer_match, "fer_match_detail": fer_detail, "per_point": per_point,
         }

@@ -109,6 +109,25 @@ typedef struct {
 bch_status bch_build_pcm(int n, int k, bch_pcm_kind kind, int m_rows, uint64_t seed,
                          const bch_pcm_opts *opts, bch_code **out);
 
+/* Device-side search for H_o: step 6 of Sec. III-A (simulated annealing of the rows'
+ * cyclic shifts) run as n_chains independent chains in parallel on the GPU, one thread
+ * block per chain.  Steps 1-5 run on the host as in bch_build_pcm; chain c starts from
+ * the builder's SplitMix64 state after step 5 advanced by c x 0xD1B54A32D192ED03, so
+ * chain 0 is exactly the annealing bch_build_pcm(n, k, OPTIMIZED, m_rows, seed, opts)
+ * runs.  Every chain's matrix gets the rank repair; the kept matrix is the one with the
+ * lowest loss #4-cycles + lambda Var(column weights) among the chains that reach rank
+ * n-k (ties: the lowest chain).  The paper anneals once; running many chains is this
+ * library's use of the GPU for the step.  stats (nullable, host [n_chains][3]): each
+ * chain's 4-cycles, sum of squared column weights, and 1 if it reached rank n-k, else 0.
+ * dense_all (nullable, host, capacity bytes >= n_chains rows n): every chain's matrix,
+ * [chain][row][column] bytes.  *best (nullable) receives the kept chain.  Synchronous;
+ * allocates and frees its own device buffers.  BCH_EINVAL as bch_build_pcm, or for
+ * n_chains outside 1..4096 or more than 400 rows; BCH_ERANK if no chain reaches rank
+ * n-k.  *out is released with bch_code_free(). */
+bch_status bch_search_pcm(int n, int k, int m_rows, uint64_t seed, const bch_pcm_opts *opts,
+                          int n_chains, long long *stats, uint8_t *dense_all, size_t capacity,
+                          int *best, bch_code **out);
+
 /* Host-only variant of bch_build_pcm: runs the same construction and writes the matrix
  * as bytes (rows x n, row-major) into caller-owned host memory `dense` of `capacity`
  * bytes; *rows receives the row count.  Touches no GPU. */

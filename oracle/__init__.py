@@ -66,6 +66,7 @@ def _load():
             "or_framegen": (i, [i, i, u64, u64, i, d, d, P, i, P, P]),
             "or_draw_autos": (i, [i, i, u64, u64, i, P]),
             "or_build_ho": (i, [i, i, i, u64, i, i, d, d, d, P, P, P]),
+            "or_build_ho_chain": (i, [i, i, i, u64, i, i, d, d, d, i, P, P, P, P]),
             "or_nms_plain": (i, [P, i, i, P, i, i, i, d, i, P, P, P, P, P, P]),
             "or_nms_enhanced": (i, [P, i, i, P, i, i, i, P, i, P, i, P, P, P, P, P, P, P]),
             "or_nms_plain_f32": (i, [P, i, i, P, i, i, i, C.c_float, i, P, P, P, P]),
@@ -201,6 +202,22 @@ def build_ho(n, k, m_rows=0, seed=0x2412_20828, q_rounds=DEFAULT_Q_ROUNDS,
                                _p(H), _p(r1), _p(mo)), "build_ho")
     H = np.ascontiguousarray(H[: int(mo[0])])
     return (H, int(r1[0])) if return_r1 else H
+
+
+def build_ho_chain(n, k, chain, m_rows=0, seed=0x2412_20828, q_rounds=DEFAULT_Q_ROUNDS,
+                   sa_steps=DEFAULT_SA_STEPS, sa_lambda=None, t0_frac=DEFAULT_T0_FRAC,
+                   cool=DEFAULT_COOL):
+    """H_o annealed by chain `chain` of a parallel annealing search (see the C file;
+    chain 0 is build_ho).  Returns (H, number of 4-cycles, sum of squared column
+    weights) of the final matrix."""
+    lam = float(n) if sa_lambda is None else float(sa_lambda)
+    H = np.zeros((max(m_rows, 2 * (n - k)), n), np.uint8)
+    r1 = np.zeros(1, np.int32)
+    mo = np.zeros(1, np.int32)
+    st = np.zeros(2, np.int64)
+    _check(_load().or_build_ho_chain(n, k, m_rows, seed, q_rounds, sa_steps, lam, t0_frac, cool,
+                                     int(chain), _p(H), _p(r1), _p(mo), _p(st)), "build_ho_chain")
+    return np.ascontiguousarray(H[: int(mo[0])]), int(st[0]), int(st[1])
 
 
 # ----------------------------------------------------------------------------- decoders

@@ -570,10 +570,16 @@ static int find_row(const uint8_t *rows, int M, int n, const uint8_t *r, int ski
  *          at t0_frac * loss_0 and is multiplied by cool after every proposal;
  *  repair  if rank < n-k, rows in order try rotations q = 1..n-1 and keep the first
  *          that raises the rank, until rank = n-k; else OR_ERANK.
- * The PRNG is SplitMix64 with state `seed`, consumed in exactly that order. */
-int or_build_ho(int n, int k, int m_rows, uint64_t seed, int q_rounds, int sa_steps,
-                double sa_lambda, double sa_t0_frac, double sa_cool, uint8_t *Ho,
-                int *r1_count, int *m_rows_out) {
+ * The PRNG is SplitMix64 with state `seed`, consumed in exactly that order.
+ *
+ * or_build_ho_chain runs the same steps but anneals chain `chain` of a parallel search
+ * over annealing runs: after step 5 its PRNG state is advanced by chain x
+ * 0xD1B54A32D192ED03 (a second Weyl increment, so every chain draws its own stream);
+ * chain 0 is or_build_ho itself.  Optional stats[2]: the final matrix's number of
+ * 4-cycles and sum of squared column weights. */
+int or_build_ho_chain(int n, int k, int m_rows, uint64_t seed, int q_rounds, int sa_steps,
+                      double sa_lambda, double sa_t0_frac, double sa_cool, int chain, uint8_t *Ho,
+                      int *r1_count, int *m_rows_out, long long *stats) {
   int M = n - k;
   int want_default = m_rows <= 0;
   if (want_default) m_rows = 2 * M;
@@ -689,7 +695,8 @@ int or_build_ho(int n, int k, int m_rows, uint64_t seed, int q_rounds, int sa_st
   free(ord);
   rl_free(&cur);
 
-  /* step 6: simulated annealing over cyclic row shifts */
+  /* step 6: simulated annealing over cyclic row shifts (chain `chain`) */
+  st += (uint64_t)chain * 0xD1B54A32D192ED03ULL;
   int Mo = m_rows;
   long long *ov = (long long *)malloc(sizeof(long long) * (size_t)Mo * Mo);
   long long *cyc = (long long *)malloc(sizeof(long long) * (size_t)Mo);
@@ -792,7 +799,26 @@ int or_build_ho(int n, int k, int m_rows, uint64_t seed, int q_rounds, int sa_st
   }
   free(tmp);
   if (rk != M) return OR_ERANK;
+  if (stats) { /* 4-cycles and column-weight square sum of the final matrix */
+    long long c4 = 0, ss = 0;
+    for (int r = 0; r < Mo; r++)
+      for (int r2 = r + 1; r2 < Mo; r2++) c4 += c2(overlap(H + (size_t)r * n, H + (size_t)r2 * n, n));
+    for (int i = 0; i < n; i++) {
+      long long w = 0;
+      for (int r = 0; r < Mo; r++) w += H[(size_t)r * n + i];
+      ss += w * w;
+    }
+    stats[0] = c4;
+    stats[1] = ss;
+  }
   return OR_OK;
+}
+
+int or_build_ho(int n, int k, int m_rows, uint64_t seed, int q_rounds, int sa_steps,
+                double sa_lambda, double sa_t0_frac, double sa_cool, uint8_t *Ho,
+                int *r1_count, int *m_rows_out) {
+  return or_build_ho_chain(n, k, m_rows, seed, q_rounds, sa_steps, sa_lambda, sa_t0_frac, sa_cool,
+                           0, Ho, r1_count, m_rows_out, NULL);
 }
 
 /* ------------------------------------------------------------------------------

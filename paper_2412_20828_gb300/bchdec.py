@@ -23,7 +23,7 @@ FLAG_CONVERGED, FLAG_OSD = 1, 2
 
 # Every symbol the header declares (checked by the tests without a GPU).
 EXPORTS = (
-    "bch_build_pcm", "bch_build_pcm_host", "bch_nms_kernel_info", "bch_nms_jit_check", "bch_code_info", "bch_pcm_export", "bch_code_free",
+    "bch_build_pcm", "bch_build_pcm_host", "bch_search_pcm", "bch_nms_kernel_info", "bch_nms_jit_check", "bch_code_info", "bch_pcm_export", "bch_code_free",
     "bch_draw_automorphisms", "bch_draw_automorphisms_host", "bch_gen_frames",
     "bch_workspace_size", "bch_nms_decode", "bch_hybrid_decode", "bch_hybrid_decode_noalloc",
     "bch_osd_decode",
@@ -107,6 +107,8 @@ def load():
         sig = {
             "bch_build_pcm": (st, [i, i, i, i, u64, C.POINTER(PcmOpts), C.POINTER(P)]),
             "bch_build_pcm_host": (st, [i, i, i, i, u64, C.POINTER(PcmOpts), P, sz, C.POINTER(i)]),
+            "bch_search_pcm": (st, [i, i, i, u64, C.POINTER(PcmOpts), i, P, P, sz, C.POINTER(i),
+                                    C.POINTER(P)]),
             "bch_nms_kernel_info": (st, [P, i, i, C.c_char_p, sz]),
             "bch_nms_jit_check": (st, [i, i, i, u64, P, i, C.c_char_p, sz]),
             "bch_code_info": (st, [P, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i),
@@ -207,6 +209,17 @@ class Code:
         self.n, self.k, self.rows, self.edges, self.max_row_weight = (x.value for x in a)
         self.kind = kind
 
+    @classmethod
+    def _adopt(cls, handle, kind):
+        """Wraps a code object the library created (ownership passes to the wrapper)."""
+        self = cls.__new__(cls)
+        self._h = handle
+        a = [C.c_int() for _ in range(5)]
+        _check(load().bch_code_info(self._h, *[C.byref(x) for x in a]), "bch_code_info")
+        self.n, self.k, self.rows, self.edges, self.max_row_weight = (x.value for x in a)
+        self.kind = kind
+        return self
+
     @property
     def handle(self):
         return self._h
@@ -231,6 +244,26 @@ class Code:
             self.close()
         except Exception:
             pass
+
+
+def search_pcm(n, k, n_chains, m_rows=0, seed=0x2412_20828, q_rounds=4, sa_steps=20000,
+               sa_lambda=0.0, sa_t0_frac=0.05, sa_cool=0.9995, return_all=False):
+    """bch_search_pcm: the annealing step of H_o as n_chains parallel chains on the GPU;
+    returns (Code of the kept chain, kept chain, stats [n_chains][3]) and, with
+    return_all, every chain's matrix [n_chains][rows][n]."""
+    rows = max(m_rows, 2 * (n - k))  # capacity; the matrices are [n_chains][rows of H_o][n]
+    stats = np.zeros((n_chains, 3), np.int64)
+    dense = np.zeros(n_chains * rows * n, np.uint8) if return_all else None
+    best = C.c_int(-1)
+    h = C.c_void_p()
+    opts = PcmOpts(q_rounds, sa_steps, sa_lambda, sa_t0_frac, sa_cool)
+    _check(load().bch_search_pcm(n, k, m_rows, seed, C.byref(opts), n_chains, _ptr(stats),
+                                 _ptr(dense), dense.nbytes if dense is not None else 0,
+                                 C.byref(best), C.byref(h)), "bch_search_pcm")
+    code = Code._adopt(h, PCM_OPTIMIZED)
+    if return_all:
+        return code, best.value, stats, dense[: n_chains * code.rows * n].reshape(n_chains, code.rows, n)
+    return code, best.value, stats
 
 
 def build_pcm(n, k, kind=PCM_OPTIMIZED, m_rows=0, seed=0x2412_20828, **opts) -> Code:

@@ -21,7 +21,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["k_nms.cu", "k_nms_fp32.cu", "k_nms_fp16.cu", "k_nms_int8.cu", "k_osd.cu", "k_misc.cu",
-              "k_train.cu", "capi.cu", "runtime.cu", "noalloc.cu", "serve.cu"]
+              "k_train.cu", "k_search.cu", "capi.cu", "runtime.cu", "noalloc.cu", "serve.cu"]
 CPP_SOURCES = ["bch_host.cpp", "jit.cpp"]
 
 

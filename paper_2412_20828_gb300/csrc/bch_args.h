@@ -45,6 +45,17 @@ struct BwdArgs {
   float alpha[32];
 };
 
+// Parallel annealing chains of the H_o search (one block per chain).
+struct AnnealArgs {
+  int n, Mo, steps, chains;
+  double lam, T0, cool;            // loss weight, start temperature, cooling factor
+  const ulonglong2 *rows0;         // [Mo] rows after step 5 (bits 0..63, 64..127)
+  const uint64_t *state0;          // [chains] SplitMix64 states
+  ulonglong2 *rows_out;            // [chains][Mo] annealed rows
+};
+cudaError_t launch_anneal(const AnnealArgs &a, cudaStream_t st);
+size_t anneal_smem_bytes(int Mo);
+
 // Resident blocks per SM and SM count for (fn, block size, dynamic shared memory) on the
 // current device; raises the kernel's shared-memory limit when this launch needs more
 // than any before.  Remembered per combination, so repeated launches cost no driver

@@ -280,8 +280,11 @@ long long pairs(long long x) { return x * (x - 1) / 2; }
 
 }  // namespace
 
-bch_status build_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoOptions &opt,
-                    std::vector<Row> *rows_out, int *r1_count, std::string *err) {
+// Steps 2-5 of the H_o construction: the padded row list and the PRNG state after the
+// padding (the state the annealing of step 6 continues from).
+bch_status prepare_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoOptions &opt,
+                      std::vector<Row> *rows_out, uint64_t *state_out, int *r1_count,
+                      std::string *err) {
   const int n = alg.n, M = alg.n - alg.k;
   const bool want_default = m_rows <= 0;
   if (want_default) m_rows = 2 * M;
@@ -353,8 +356,32 @@ bch_status build_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoO
       }
     }
   }
-  // step 6: simulated annealing over cyclic row shifts
-  const int Mo = m_rows;
+  *rows_out = std::move(Ho);
+  *state_out = st;
+  return BCH_OK;
+}
+
+// Loss terms of a row list: number of 4-cycles (row pairs' overlaps taken two at a
+// time), sum of squared column weights, number of edges.
+void ho_loss_terms(int n, const std::vector<Row> &Ho, long long *C4, long long *SS, long long *E) {
+  const int Mo = int(Ho.size());
+  long long c4 = 0, ss = 0, e = 0;
+  for (int r = 0; r < Mo; r++)
+    for (int r2 = r + 1; r2 < Mo; r2++) c4 += pairs((Ho[r] & Ho[r2]).weight());
+  for (int i = 0; i < n; i++) {
+    long long w = 0;
+    for (int r = 0; r < Mo; r++) w += Ho[r].get(i) ? 1 : 0;
+    ss += w * w;
+    e += w;
+  }
+  *C4 = c4;
+  *SS = ss;
+  *E = e;
+}
+
+// Step 6: simulated annealing of the rows' cyclic shifts, PRNG state `st`.
+void anneal_ho(int n, std::vector<Row> &Ho, uint64_t st, const HoOptions &opt) {
+  const int Mo = int(Ho.size());
   const double lam = opt.sa_lambda > 0.0 ? opt.sa_lambda : double(n);
   std::vector<long long> ov(size_t(Mo) * Mo, 0), cyc(Mo, 0), nov(Mo, 0);
   std::vector<long long> colw(n, 0);
@@ -434,7 +461,12 @@ bch_status build_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoO
     }
     T *= opt.sa_cool;
   }
-  // rank repair
+}
+
+// Rank repair: rows in order try the rotations q = 1 .. n-1 and keep the first that
+// raises the rank, until the rank is n - k.  False if it stays below.
+bool repair_rank(int n, int M, std::vector<Row> &Ho) {
+  const int Mo = int(Ho.size());
   int rk = gf2_rank(Ho, n);
   for (int r = 0; r < Mo && rk < M; r++) {
     for (int q = 1; q < n; q++) {
@@ -450,7 +482,17 @@ bch_status build_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoO
       }
     }
   }
-  if (rk != M) {
+  return rk == M;
+}
+
+bch_status build_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoOptions &opt,
+                    std::vector<Row> *rows_out, int *r1_count, std::string *err) {
+  std::vector<Row> Ho;
+  uint64_t st = 0;
+  bch_status s = prepare_ho(alg, m_rows, seed, opt, &Ho, &st, r1_count, err);
+  if (s != BCH_OK) return s;
+  anneal_ho(alg.n, Ho, st, opt);
+  if (!repair_rank(alg.n, alg.n - alg.k, Ho)) {
     *err = "H_o did not reach rank n-k";
     return BCH_ERANK;
   }

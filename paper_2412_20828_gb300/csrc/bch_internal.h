@@ -63,6 +63,14 @@ struct HoOptions {
 bch_status build_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoOptions &opt,
                     std::vector<Row> *rows, int *r1_count, std::string *err);
 
+// The construction split in its parts (build_ho = prepare, anneal, repair): steps 2-5
+// (rows and the PRNG state after the padding), step 6 from a given state, rank repair.
+bch_status prepare_ho(const CodeAlgebra &alg, int m_rows, uint64_t seed, const HoOptions &opt,
+                      std::vector<Row> *rows, uint64_t *state, int *r1_count, std::string *err);
+void anneal_ho(int n, std::vector<Row> &Ho, uint64_t state, const HoOptions &opt);
+bool repair_rank(int n, int M, std::vector<Row> &Ho);
+void ho_loss_terms(int n, const std::vector<Row> &Ho, long long *C4, long long *SS, long long *E);
+
 int gf2_rank(std::vector<Row> rows, int n);
 
 uint64_t splitmix64_next(uint64_t *state);

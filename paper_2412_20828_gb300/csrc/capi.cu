@@ -335,6 +335,18 @@ const char *bch_version(void) { return "bchdec-gb300 1.0 (sm_103a)"; }
 
 unsigned long long bch_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+static HoOptions ho_options(const bch_pcm_opts *opts) {
+  HoOptions o;
+  if (opts) {
+    if (opts->q_rounds >= 0) o.q_rounds = opts->q_rounds;
+    if (opts->sa_steps >= 0) o.sa_steps = opts->sa_steps;
+    o.sa_lambda = opts->sa_lambda;
+    if (opts->sa_t0_frac > 0) o.sa_t0_frac = opts->sa_t0_frac;
+    if (opts->sa_cool > 0) o.sa_cool = opts->sa_cool;
+  }
+  return o;
+}
+
 static bch_status build_host(int n, int k, bch_pcm_kind kind, int m_rows, uint64_t seed,
                              const bch_pcm_opts *opts, bch_code *c) {
   std::string err;
@@ -345,14 +357,7 @@ static bch_status build_host(int n, int k, bch_pcm_kind kind, int m_rows, uint64
     return BCH_OK;
   }
   if (kind != BCH_PCM_OPTIMIZED) return fail(BCH_EINVAL, "unknown pcm kind");
-  HoOptions o;
-  if (opts) {
-    if (opts->q_rounds >= 0) o.q_rounds = opts->q_rounds;
-    if (opts->sa_steps >= 0) o.sa_steps = opts->sa_steps;
-    o.sa_lambda = opts->sa_lambda;
-    if (opts->sa_t0_frac > 0) o.sa_t0_frac = opts->sa_t0_frac;
-    if (opts->sa_cool > 0) o.sa_cool = opts->sa_cool;
-  }
+  const HoOptions o = ho_options(opts);
   bch_status s = build_ho(c->alg, m_rows, seed, o, &c->rows, &c->r1_count, &err);
   if (s != BCH_OK) return fail(s, err);
   return BCH_OK;
@@ -369,6 +374,97 @@ bch_status bch_build_pcm_host(int n, int k, bch_pcm_kind kind, int m_rows, uint6
   for (size_t r = 0; r < c.rows.size(); r++)
     for (int i = 0; i < n; i++) dense[r * n + i] = c.rows[r].get(i) ? 1 : 0;
   *rows = int(c.rows.size());
+  return BCH_OK;
+}
+
+bch_status bch_search_pcm(int n, int k, int m_rows, uint64_t seed, const bch_pcm_opts *opts,
+                          int n_chains, long long *stats, uint8_t *dense_all, size_t capacity,
+                          int *best, bch_code **out) {
+  if (!out) return fail(BCH_EINVAL, "out is null");
+  *out = nullptr;
+  if (n_chains < 1 || n_chains > 4096) return fail(BCH_EINVAL, "n_chains must be in [1, 4096]");
+  std::unique_ptr<bch_code> c(new (std::nothrow) bch_code());
+  if (!c) return fail(BCH_ENOMEM, "host allocation");
+  std::string err;
+  if (!make_algebra(n, k, &c->alg, &err)) return fail(BCH_EINVAL, err);
+  c->kind = BCH_PCM_OPTIMIZED;
+  const HoOptions o = ho_options(opts);
+  std::vector<Row> H0;
+  uint64_t st0 = 0;
+  bch_status s = prepare_ho(c->alg, m_rows, seed, o, &H0, &st0, &c->r1_count, &err);
+  if (s != BCH_OK) return fail(s, err);
+  const int Mo = int(H0.size()), M = n - k;
+  if (Mo > 400) return fail(BCH_EINVAL, "the device search holds at most 400 rows");
+  if (dense_all && capacity < size_t(n_chains) * Mo * n) return fail(BCH_EINVAL, "dense_all too small");
+  // start temperature exactly as the host annealing computes it
+  long long C4 = 0, SS = 0, E = 0;
+  ho_loss_terms(n, H0, &C4, &SS, &E);
+  const double lam = o.sa_lambda > 0.0 ? o.sa_lambda : double(n);
+  const double loss0 = double(C4) + lam * (double(SS) - double(E) * double(E) / double(n)) / double(n);
+  std::vector<ulonglong2> rows0(Mo);
+  for (int r = 0; r < Mo; r++) rows0[r] = make_ulonglong2(H0[r].w[0], H0[r].w[1]);
+  std::vector<uint64_t> states(n_chains);
+  for (int ch = 0; ch < n_chains; ch++) states[ch] = st0 + uint64_t(ch) * 0xD1B54A32D192ED03ULL;
+  ulonglong2 *d_rows0 = nullptr, *d_out = nullptr;
+  uint64_t *d_st = nullptr;
+  std::vector<ulonglong2> rows_out(size_t(n_chains) * Mo);
+  cudaError_t e = cudaMalloc(&d_rows0, size_t(Mo) * sizeof(ulonglong2));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, rows_out.size() * sizeof(ulonglong2));
+  if (e == cudaSuccess) e = cudaMalloc(&d_st, size_t(n_chains) * 8);
+  if (e == cudaSuccess) e = cudaMemcpy(d_rows0, rows0.data(), size_t(Mo) * sizeof(ulonglong2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_st, states.data(), size_t(n_chains) * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    AnnealArgs a;
+    a.n = n;
+    a.Mo = Mo;
+    a.steps = o.sa_steps;
+    a.chains = n_chains;
+    a.lam = lam;
+    a.T0 = o.sa_t0_frac * loss0;
+    a.cool = o.sa_cool;
+    a.rows0 = d_rows0;
+    a.state0 = d_st;
+    a.rows_out = d_out;
+    e = launch_anneal(a, nullptr);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(rows_out.data(), d_out, rows_out.size() * sizeof(ulonglong2), cudaMemcpyDeviceToHost);
+  cudaFree(d_rows0);
+  cudaFree(d_out);
+  cudaFree(d_st);
+  if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("annealing chains: ") + cudaGetErrorString(e));
+  int kept = -1;
+  double kept_loss = 0.0;
+  std::vector<Row> best_rows;
+  for (int ch = 0; ch < n_chains; ch++) {
+    std::vector<Row> Hc(Mo);
+    for (int r = 0; r < Mo; r++) {
+      Hc[r].w[0] = rows_out[size_t(ch) * Mo + r].x;
+      Hc[r].w[1] = rows_out[size_t(ch) * Mo + r].y;
+    }
+    const bool ok = repair_rank(n, M, Hc);
+    long long c4 = 0, ss = 0, e2 = 0;
+    ho_loss_terms(n, Hc, &c4, &ss, &e2);
+    if (stats) {
+      stats[size_t(ch) * 3] = c4;
+      stats[size_t(ch) * 3 + 1] = ss;
+      stats[size_t(ch) * 3 + 2] = ok ? 1 : 0;
+    }
+    if (dense_all)
+      for (int r = 0; r < Mo; r++)
+        for (int i = 0; i < n; i++) dense_all[(size_t(ch) * Mo + r) * n + i] = Hc[r].get(i) ? 1 : 0;
+    const double loss = double(c4) + lam * (double(ss) - double(e2) * double(e2) / double(n)) / double(n);
+    if (ok && (kept < 0 || loss < kept_loss)) {
+      kept = ch;
+      kept_loss = loss;
+      best_rows = Hc;
+    }
+  }
+  if (kept < 0) return fail(BCH_ERANK, "no annealing chain reached rank n-k");
+  if (best) *best = kept;
+  c->rows = std::move(best_rows);
+  s = upload_code(c.get());
+  if (s != BCH_OK) return s;
+  *out = c.release();
   return BCH_OK;
 }
 
