@@ -343,11 +343,13 @@ static void emit_serve_copy(std::ostringstream &o, const bch_code *c, const std:
 // (partials to buffer A or B), a barrier, the second pass (combine, output pass), and
 // finally scatter the half's row sums.  Both halves are emitted from the same chunk
 // list, so they pass the same barriers.
-static void emit_split_half(std::ostringstream &o, const bch_code *c, int msg, int h, int R) {
+static void emit_split_half(std::ostringstream &o, const bch_code *c, int msg, int h, int R,
+                            const std::string &prefix = "split_half") {
   const int n = c->alg.n, m = c->alg.m;
   const int u0 = 64 * h, u1 = std::min(n, 64 * h + 64), nh = u1 - u0;
   const int nwh = (nh + 31) / 32;
-  o << "__device__ " << (std::getenv("BCHDEC_JIT_SPLIT_NOINLINE") ? "__noinline__" : "__forceinline__") << " void split_half" << h << "(StoreT<" << msg << ">::Y *y, StoreT<" << msg
+  o << "__device__ " << (std::getenv("BCHDEC_JIT_SPLIT_NOINLINE") ? "__noinline__" : "__forceinline__") << " void "
+    << prefix << h << "(StoreT<" << msg << ">::Y *y, StoreT<" << msg
     << ">::A *acc, float2 *pa, float2 *pb, uint32_t jr, uint32_t sp, float alpha) {\n"
     << "#undef BCH_SV\n#define BCH_SV(u) S[u]\n#undef BCH_H\n#define BCH_H " << h << "\n"
     << "  BCH_VT z[" << nh << "];\n"
@@ -435,6 +437,49 @@ static std::string jit_split_source(const bch_code *c, int msg) {
     << "  extern __shared__ __align__(16) unsigned char smem[];\n"
     << "  bchlib::nms_split_persistent<" << msg << ", " << G << ">(a, smem, bchlib::SplitCopy(), "
     << (M + R - 1) / R << ", " << R << ");\n}\n";
+  return o.str();
+}
+
+// The block-bound serving kernel for a server's codes (FP32): per code a session with
+// the batch kernels' mapping -- for n <= 63 the one-thread-per-frame copy functor on
+// columns of stride 256, for n = 127 the two split halves -- and a dispatcher on the
+// code a block is bound to.
+std::string jit_serve_blocks_source(const bch_code *const *codes, int n_codes) {
+  const int R = jit_split_chunk_rows();
+  std::ostringstream o;
+  emit_prologue(o, 0, true);
+  o << split_macros(0) << "#define BCH_FS 128\n#define BCH_TPB 256\n";
+  for (int i = 0; i < n_codes; i++) {
+    const bch_code *c = codes[i];
+    if (c->alg.n <= 63) {
+      emit_copy(o, c, 0, "SrvFlat" + std::to_string(i), 256, false);
+    } else {
+      const std::string pre = "srv" + std::to_string(i) + "_half";
+      emit_split_half(o, c, 0, 0, R, pre);
+      emit_split_half(o, c, 0, 1, R, pre);
+      o << "struct SrvSplit" << i << " {\n"
+        << "  __device__ __forceinline__ void operator()(int h, float *y, float *acc, float2 *pa, float2 *pb,\n"
+        << "      uint32_t jr, uint32_t sp, float alpha) const {\n"
+        << "    if (h == 0) " << pre << "0(y, acc, pa, pb, jr, sp, alpha);\n"
+        << "    else " << pre << "1(y, acc, pa, pb, jr, sp, alpha);\n  }\n};\n";
+    }
+  }
+  o << "struct SrvBlockSessions {\n  const SrvArgs &a;\n"
+    << "  __device__ __forceinline__ void operator()(int code, unsigned char *smem, const SrvBlockLayout &L) const {\n"
+    << "    switch (code) {\n";
+  for (int i = 0; i < n_codes; i++) {
+    const bch_code *c = codes[i];
+    o << "      case " << i << ": ";
+    if (c->alg.n <= 63)
+      o << "serve_session_flat<2>(a, " << i << ", smem, L, SrvFlat" << i << "()); break;\n";
+    else
+      o << "serve_session_split(a, " << i << ", smem, L, SrvSplit" << i << "(), "
+        << (int(c->rows.size()) + R - 1) / R << ", " << R << "); break;\n";
+  }
+  o << "      default: break;\n    }\n  }\n};\n}  // namespace bchlib\n"
+    << "extern \"C\" __global__ void __launch_bounds__(256, 1) bch_serve_blocks(const bchlib::SrvArgs a) {\n"
+    << "  extern __shared__ __align__(16) unsigned char smem[];\n"
+    << "  bchlib::serve_blocks(a, smem, bchlib::SrvBlockSessions{a});\n}\n";
   return o.str();
 }
 
@@ -654,6 +699,10 @@ cudaKernel_t jit_serve_kernel(const bch_code *const *codes, int n_codes, std::st
   return compile_source(jit_serve_source(codes, n_codes), "bch_serve_jit", err);
 }
 
+cudaKernel_t jit_serve_blocks_kernel(const bch_code *const *codes, int n_codes, std::string *err) {
+  return compile_source(jit_serve_blocks_source(codes, n_codes), "bch_serve_blocks", err);
+}
+
 // Compiles the specialised source with ptxas reporting on; no GPU is needed.  Returns
 // false with *log holding the compiler output on failure.
 static bool compile_check_source(const std::string &src, const char *entry, std::string *log);
@@ -663,6 +712,8 @@ bool jit_compile_check(const bch_code *c, int msg, std::string *log) {
 }
 
 bool jit_serve_compile_check(const bch_code *const *codes, int n_codes, std::string *log) {
+  if (!std::getenv("BCHDEC_SERVE_KERNEL") || std::strcmp(std::getenv("BCHDEC_SERVE_KERNEL"), "warps") != 0)
+    return compile_check_source(jit_serve_blocks_source(codes, n_codes), "bch_serve_blocks", log);
   return compile_check_source(jit_serve_source(codes, n_codes), "bch_serve_jit", log);
 }
 

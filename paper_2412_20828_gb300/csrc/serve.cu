@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(32) serve_kernel(const SrvArgs a) {
 // ------------------------------------------------------------------------- host side
 namespace bchlib {
 cudaKernel_t jit_serve_kernel(const bch_code *const *codes, int n_codes, std::string *err);
+cudaKernel_t jit_serve_blocks_kernel(const bch_code *const *codes, int n_codes, std::string *err);
 }  // namespace bchlib
 
 struct bch_server {
@@ -134,7 +135,7 @@ struct bch_server {
   unsigned sub_tail[kSrvMaxCodes] = {};
   unsigned comp_read = 0;
   unsigned long long next_id = 1;
-  int blocks = 0;
+  int blocks = 0, threads = 32;
   size_t smem = 0;
   const void *kfn = nullptr;  // the serving kernel: specialised to the codes, or precompiled
   std::string kinfo;
@@ -233,7 +234,7 @@ bch_status launch_server_kernel(bch_server *s) {
   if (e == cudaSuccess) {
     void *args[] = {&s->args};
     note_launch();
-    e = cudaLaunchKernel(s->kfn, dim3(unsigned(s->blocks)), dim3(32u), args, s->smem, s->kst);
+    e = cudaLaunchKernel(s->kfn, dim3(unsigned(s->blocks)), dim3(unsigned(s->threads)), args, s->smem, s->kst);
   }
   if (e != cudaSuccess) {
     s->sh->running = 0;
@@ -515,12 +516,35 @@ bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
   // scratch, automorphism parameters [9][32], claim segments [3][32]
   s->smem = sizeof(float) * 128 * 32 * 2 + sizeof(float) * size_t(A.scr_words) * 32 + sizeof(OsdSmem) +
             sizeof(uint32_t) * 9 * 32 + sizeof(int) * 3 * 32;
+  s->threads = 32;
+  // The block-bound serving kernel (default unless BCHDEC_SERVE_KERNEL=warps or the
+  // precompiled kernel is selected): one 256-thread block per SM, bound to one code per
+  // session, with the batch kernels' mappings.
+  const char *sk = std::getenv("BCHDEC_SERVE_KERNEL");
+  if (s->kinfo == "jit" && !(sk && std::strcmp(sk, "warps") == 0)) {
+    A.blk_max_rows = 0;
+    A.blk_flat_n = 0;
+    A.blk_R = 16;
+    for (const bch_code *co : s->codes) {
+      A.blk_max_rows = std::max(A.blk_max_rows, int(co->rows.size()));
+      if (co->alg.n <= 63) A.blk_flat_n = std::max(A.blk_flat_n, co->alg.n);
+    }
+    const SrvBlockLayout BL = srv_block_layout(A.blk_max_rows, A.blk_flat_n, A.P, A.blk_R, 127);
+    std::string err;
+    cudaKernel_t k = BL.total <= 227 * 1024 ? jit_serve_blocks_kernel(s->codes.data(), cfg->n_codes, &err) : nullptr;
+    if (k) {
+      s->kfn = reinterpret_cast<const void *>(k);
+      s->kinfo = "jit-blocks";
+      s->smem = BL.total;
+      s->threads = kSrvBlockThreads;
+    }
+  }
   int sms = 0, per_sm = 0;
-  if (launch_geometry(s->kfn, 32, s->smem, &sms, &per_sm) != cudaSuccess || per_sm < 1) {
+  if (launch_geometry(s->kfn, s->threads, s->smem, &sms, &per_sm) != cudaSuccess || per_sm < 1) {
     cleanup();
     return fail(BCH_ECUDA, "serve kernel attributes");
   }
-  s->blocks = cfg->warps > 0 ? cfg->warps : sms * per_sm;
+  s->blocks = s->threads > 32 ? sms : (cfg->warps > 0 ? cfg->warps : sms * per_sm);
   cudaDeviceSynchronize();
   *out = s;
   return BCH_OK;

@@ -51,15 +51,22 @@ def _drain(srv, want):
     raise AssertionError("server did not complete the requests")
 
 
-@pytest.mark.parametrize("kernel", ["jit", "generic"])
+@pytest.mark.parametrize("kernel", ["blocks", "warps", "generic"])
 def test_results_alone_and_in_mix_match_batch_decoder(setup, monkeypatch, kernel):
+    """blocks: the block-bound kernel (sessions per code with the batch mappings, the
+    default); warps: the per-warp kernel with lane refill; generic: the precompiled one."""
     torch, codes, stds = setup
-    monkeypatch.setenv("BCHDEC_NMS_KERNEL", kernel)
+    if kernel == "generic":
+        monkeypatch.setenv("BCHDEC_NMS_KERNEL", "generic")
+    if kernel == "warps":
+        monkeypatch.setenv("BCHDEC_SERVE_KERNEL", "warps")
     srv = B.Server(codes, stds, 12, 0.78, budget_bytes=1 << 30, max_requests=256)
-    monkeypatch.delenv("BCHDEC_NMS_KERNEL")
+    monkeypatch.delenv("BCHDEC_NMS_KERNEL", raising=False)
+    monkeypatch.delenv("BCHDEC_SERVE_KERNEL", raising=False)
     try:
         info = srv.kernel_info()
-        assert info == "jit" if kernel == "jit" else info.startswith("generic")
+        assert info == {"blocks": "jit-blocks", "warps": "jit"}.get(kernel, info) and (
+            kernel != "generic" or info.startswith("generic"))
         reqs = []
         for i, (n, k) in enumerate(CODES):
             for j, (F, e) in enumerate([(37, 2.0), (300, 3.0), (1, 4.0)]):
