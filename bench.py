@@ -231,6 +231,11 @@ def run_serving(B, torch, dev, seconds, rate):
     res_sub = B.serve_bench(srv, codes, stds, pools, sub, seconds, seed=13)
     stat_sub = B.serve_bench(None, codes, stds, pools, sub, seconds, seed=13, static_batching=True,
                              batch_us=1000, batch_frames=65536)
+    # capacity: both modes offered twice the configured rate (above what either serves)
+    progress("serving: capacity at twice the configured rate")
+    res_cap = B.serve_bench(srv, codes, stds, pools, 2 * rate, seconds, seed=14)
+    stat_cap = B.serve_bench(None, codes, stds, pools, 2 * rate, seconds, seed=14, static_batching=True,
+                             batch_us=1000, batch_frames=65536)
     stats = srv.stats()
     srv.close()
     # the single plain decoder (standard matrix, 8 iterations, no automorphisms, no OSD)
@@ -245,6 +250,7 @@ def run_serving(B, torch, dev, seconds, rate):
                         "(63,36),(63,45),(127,64),(127,99), Eb/N0 U[1,6] dB, hybrid NMS(12,P=3)+OSD(2)",
             "seconds": seconds, "server_kernel": server_kernel, "server": res, "static_batching": stat,
             "below_saturation": {"rate_rps": sub, "server": res_sub, "static_batching": stat_sub},
+            "twice_the_rate": {"rate_rps": 2 * rate, "server": res_cap, "static_batching": stat_cap},
             "static_batching_plain_nms": plain,
             "server_stats": stats}
 

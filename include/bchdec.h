@@ -354,7 +354,7 @@ typedef struct {
 
 typedef struct {
   long long submitted, admitted, queued, completed, kernel_launches;
-  long long bytes_in_use, pending, in_flight;
+  long long bytes_in_use, pending, in_flight, cancelled;
 } bch_server_stats;
 
 bch_status bch_server_create(const bch_server_config *cfg, bch_server **out);
@@ -377,6 +377,13 @@ bch_status bch_server_poll(bch_server *srv, uint64_t *done_ids, int max_ids, int
 bch_status bch_server_fetch(bch_server *srv, uint64_t request_id, uint64_t *hard,
                             uint8_t *iters, uint8_t *flags);
 bch_status bch_server_get_stats(bch_server *srv, bch_server_stats *out);
+/* Cancels a request: one still queued is dropped at once; one already on the GPU keeps
+ * its frames in flight and is released (memory and slot) when the kernel completes it,
+ * without being reported by bch_server_poll; a completed request not yet fetched is
+ * released at once.  Either way bch_server_fetch of its id then returns BCH_EINVAL.
+ * BCH_EINVAL for an unknown (or already cancelled) id.  No counterpart in the paper:
+ * request management of the serving loop. */
+bch_status bch_server_cancel(bch_server *srv, uint64_t request_id);
 /* Names the serving kernel the server runs: "jit" -- compiled at server creation
  * (NVRTC) with every code's rows as straight-line code, one automorphism copy per code
  * as in the batch decoder's specialised kernel, cached in the process and on disk
@@ -460,6 +467,28 @@ bch_status bch_bce_loss(int n, const float *y, int ld, const uint64_t *codeword,
 bch_status bch_train_alpha(const bch_code *code, int n_autos, int iters, float *alpha_inout,
                            int steps, int batch, float ebn0_lo, float ebn0_hi, uint64_t seed,
                            float lr, float *loss_hist, void *stream);
+
+/* Training state for resuming bch_train_alpha: the Adam moments of every factor and the
+ * number of steps taken (which also fixes the frames of the next step: step s decodes
+ * frames s batch ... (s + 1) batch - 1 of the simulated stream).  Plain data: a caller
+ * saves it with alpha[] and restores both to continue where it stopped.  A zeroed state
+ * (step = 0) starts fresh.  No counterpart in the paper: checkpointing of the training
+ * loop. */
+typedef struct {
+  int iters, batch;  /* shape the state belongs to */
+  long long step;    /* Adam steps taken */
+  double m[32], v[32];
+} bch_adam_state;
+
+/* bch_train_alpha continued from (alpha_inout, *state): runs `steps` more Adam steps
+ * and updates both after every step (so an interrupted run keeps a consistent pair).
+ * state NULL behaves as bch_train_alpha.  N steps in one call and the same N split
+ * over several calls that pass the state on give bit-identical alpha and losses.
+ * BCH_EINVAL if a nonzero state belongs to another iters or batch. */
+bch_status bch_train_alpha_resume(const bch_code *code, int n_autos, int iters, float *alpha_inout,
+                                  bch_adam_state *state, int steps, int batch, float ebn0_lo,
+                                  float ebn0_hi, uint64_t seed, float lr, float *loss_hist,
+                                  void *stream);
 
 /* ---------------------------------------------------------------- misc */
 

@@ -29,10 +29,10 @@ EXPORTS = (
     "bch_osd_decode",
     "bch_compact_failed", "bch_count_errors", "bch_nms_forward_train", "bch_nms_backward", "bch_bce_loss",
     "bch_train_alpha", "bch_decoder_create", "bch_decoder_run_host", "bch_decoder_destroy",
-    "bch_decoder_set_timing", "bch_decoder_get_timing", "bch_decoder_set_in_place",
+    "bch_decoder_set_timing", "bch_decoder_get_timing", "bch_decoder_set_in_place", "bch_train_alpha_resume",
     "bch_kernel_launches",
     "bch_server_create", "bch_server_submit", "bch_server_poll", "bch_server_fetch",
-    "bch_server_get_stats", "bch_server_kernel_info", "bch_serve_jit_check", "bch_server_destroy",
+    "bch_server_get_stats", "bch_server_cancel", "bch_server_kernel_info", "bch_serve_jit_check", "bch_server_destroy",
     "bch_serve_bench",
     "bch_status_str", "bch_last_error", "bch_version",
 )
@@ -61,7 +61,7 @@ class ServerConfig(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(nm, C.c_longlong) for nm in ("submitted", "admitted", "queued", "completed",
                                                "kernel_launches", "bytes_in_use", "pending",
-                                               "in_flight")]
+                                               "in_flight", "cancelled")]
 
 
 class ServeBenchConfig(C.Structure):
@@ -131,6 +131,7 @@ def load():
             "bch_nms_backward": (st, [P, C.POINTER(NmsParams), P, P, i, i, P, P, P, P, P]),
             "bch_bce_loss": (st, [i, P, i, P, i, P, P, P, P]),
             "bch_train_alpha": (st, [P, i, i, P, i, i, f, f, u64, f, P, P]),
+            "bch_train_alpha_resume": (st, [P, i, i, P, C.POINTER(AdamState), i, i, f, f, u64, f, P, P]),
             "bch_decoder_create": (st, [P, P, C.POINTER(NmsParams), i, i, C.POINTER(P)]),
             "bch_decoder_run_host": (st, [P, P, i, u64, u64, P, P, P]),
             "bch_decoder_destroy": (None, [P]),
@@ -143,6 +144,7 @@ def load():
             "bch_server_poll": (st, [P, P, i, C.POINTER(i), i]),
             "bch_server_fetch": (st, [P, u64, P, P, P]),
             "bch_server_get_stats": (st, [P, C.POINTER(ServerStats)]),
+            "bch_server_cancel": (st, [P, u64]),
             "bch_server_kernel_info": (st, [P, C.c_char_p, sz]),
             "bch_serve_jit_check": (st, [i, C.POINTER(C.c_int), C.POINTER(C.c_int), u64, C.c_char_p, sz]),
             "bch_server_destroy": (None, [P]),
@@ -450,6 +452,49 @@ def train_alpha(code: Code, n_autos, iters, alpha, steps, batch, ebn0_lo, ebn0_h
     return al, hist[:steps]
 
 
+class AdamState(C.Structure):
+    """bch_adam_state: the training loop's resumable state."""
+    _fields_ = [("iters", C.c_int), ("batch", C.c_int), ("step", C.c_longlong),
+                ("m", C.c_double * 32), ("v", C.c_double * 32)]
+
+    def to_arrays(self) -> dict:
+        return {"iters": self.iters, "batch": self.batch, "step": self.step,
+                "m": np.array(self.m[:]), "v": np.array(self.v[:])}
+
+    @classmethod
+    def from_arrays(cls, d) -> "AdamState":
+        s = cls()
+        s.iters, s.batch, s.step = int(d["iters"]), int(d["batch"]), int(d["step"])
+        for t in range(32):
+            s.m[t] = float(d["m"][t])
+            s.v[t] = float(d["v"][t])
+        return s
+
+
+def save_training(path, alpha, state: AdamState):
+    """Writes alpha and the Adam state to an .npz file (exact doubles and floats)."""
+    d = state.to_arrays()
+    np.savez(path, alpha=np.asarray(alpha, np.float32), **d)
+
+
+def load_training(path):
+    """(alpha, AdamState) from a file written by save_training."""
+    with np.load(path) as z:
+        return z["alpha"].copy(), AdamState.from_arrays(z)
+
+
+def train_alpha_resume(code, n_autos, iters, alpha, state, steps, batch, ebn0_lo, ebn0_hi, seed, lr,
+                       stream=None):
+    """bch_train_alpha_resume: continues from (alpha, state); returns (alpha, losses) and
+    updates state in place."""
+    al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float32), (iters,))).copy()
+    hist = np.zeros(max(steps, 1), np.float32)
+    _check(load().bch_train_alpha_resume(code.handle, n_autos, iters, _ptr(al), C.byref(state), steps,
+                                         batch, float(ebn0_lo), float(ebn0_hi), seed, float(lr),
+                                         _ptr(hist), _stream(stream)), "bch_train_alpha_resume")
+    return al, hist[:steps]
+
+
 class DecoderTiming(C.Structure):
     _fields_ = [("calls", C.c_longlong), ("chunks", C.c_longlong), ("in_place_chunks", C.c_longlong),
                 ("ms_wall", C.c_double),
@@ -541,13 +586,16 @@ class Server:
         return [int(x) for x in ids[: nd.value]]
 
     def fetch(self, rid):
-        llr, code_id, F = self._keep.pop(rid)
+        if rid not in self._keep:  # unknown, cancelled or already fetched
+            raise BchError(EINVAL, "bch_server_fetch", "request not complete or unknown")
+        llr, code_id, F = self._keep[rid]
         n = self.codes[code_id].n
         hard = np.zeros((F, (n + 63) // 64), np.uint64)
         it = np.zeros(F, np.uint8)
         fl = np.zeros(F, np.uint8)
         _check(load().bch_server_fetch(self._h, rid, _ptr(hard), _ptr(it), _ptr(fl)),
                "bch_server_fetch")
+        del self._keep[rid]
         return hard.view(np.int64), it, fl
 
     def kernel_info(self) -> str:
@@ -555,6 +603,12 @@ class Server:
         buf = C.create_string_buffer(4096)
         _check(load().bch_server_kernel_info(self._h, buf, 4096), "bch_server_kernel_info")
         return buf.value.decode()
+
+    def cancel(self, rid):
+        """bch_server_cancel: drops a queued request, or releases one on the GPU when the
+        kernel completes it (it is then never reported by poll)."""
+        _check(load().bch_server_cancel(self._h, C.c_uint64(rid)), "bch_server_cancel")
+        self._keep.pop(rid, None)
 
     def stats(self):
         st = ServerStats()

@@ -837,9 +837,18 @@ bch_status bch_bce_loss(int n, const float *y, int ld, const uint64_t *codeword,
 bch_status bch_train_alpha(const bch_code *code, int n_autos, int iters, float *alpha_inout, int steps,
                            int batch, float ebn0_lo, float ebn0_hi, uint64_t seed, float lr,
                            float *loss_hist, void *stream) {
+  return bch_train_alpha_resume(code, n_autos, iters, alpha_inout, nullptr, steps, batch, ebn0_lo, ebn0_hi,
+                                seed, lr, loss_hist, stream);
+}
+
+bch_status bch_train_alpha_resume(const bch_code *code, int n_autos, int iters, float *alpha_inout,
+                                  bch_adam_state *state, int steps, int batch, float ebn0_lo, float ebn0_hi,
+                                  uint64_t seed, float lr, float *loss_hist, void *stream) {
   if (!code_ok(code) || !alpha_inout) return fail(BCH_EINVAL, "null argument");
   if (n_autos < 1 || n_autos > 9 || iters < 1 || iters > 32 || steps < 0 || batch < 1)
     return fail(BCH_EINVAL, "bad training shape");
+  if (state && state->step != 0 && (state->iters != iters || state->step < 0 || state->batch != batch))
+    return fail(BCH_EINVAL, "the saved training state belongs to another shape (iters or batch)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int n = code->alg.n, ld = (n + 3) & ~3, W64 = (n + 63) / 64;
   const size_t fb = size_t(batch);
@@ -862,9 +871,17 @@ bch_status bch_train_alpha(const bch_code *code, int n_autos, int iters, float *
     return fail(BCH_ENOMEM, "training buffers");
   }
   std::vector<double> m1(iters, 0.0), m2(iters, 0.0);
+  long long step0 = 0;  // Adam steps (and frame batches) before this call
+  if (state && state->step > 0) {
+    step0 = state->step;
+    for (int t = 0; t < iters; t++) {
+      m1[t] = state->m[t];
+      m2[t] = state->v[t];
+    }
+  }
   const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
   bch_status s = BCH_OK;
-  for (int step = 0; step < steps && s == BCH_OK; step++) {
+  for (long long step = step0; step < step0 + steps && s == BCH_OK; step++) {
     bch_nms_params p;
     std::memset(&p, 0, sizeof(p));
     p.iters = iters;
@@ -888,13 +905,22 @@ bch_status bch_train_alpha(const bch_code *code, int n_autos, int iters, float *
       s = cuda_fail(e, "training step");
       break;
     }
-    if (loss_hist) loss_hist[step] = lv;
+    if (loss_hist) loss_hist[step - step0] = lv;
     for (int t = 0; t < iters; t++) {
       m1[t] = b1 * m1[t] + (1 - b1) * g[t];
       m2[t] = b2 * m2[t] + (1 - b2) * double(g[t]) * g[t];
-      const double mh = m1[t] / (1 - std::pow(b1, step + 1));
-      const double vh = m2[t] / (1 - std::pow(b2, step + 1));
+      const double mh = m1[t] / (1 - std::pow(b1, double(step + 1)));
+      const double vh = m2[t] / (1 - std::pow(b2, double(step + 1)));
       alpha_inout[t] = float(alpha_inout[t] - lr * mh / (std::sqrt(vh) + eps));
+    }
+    if (state) {  // kept current after every completed step
+      state->iters = iters;
+      state->batch = batch;
+      state->step = step + 1;
+      for (int t = 0; t < iters; t++) {
+        state->m[t] = m1[t];
+        state->v[t] = m2[t];
+      }
     }
   }
   cudaStreamSynchronize(st);

@@ -123,6 +123,7 @@ struct bch_server {
     size_t off = 0, bytes = 0;
     int slot = -1;
     bool done = false;
+    bool cancelled = false;  // in flight when cancelled: released on completion, not reported
   };
   std::deque<Req> pending;
   std::map<unsigned long long, Req> active;
@@ -195,6 +196,14 @@ void arena_free(bch_server *s, size_t off, size_t bytes) {
       s->free_list.erase(it);
     }
   }
+}
+
+// Returns a finished request's arena memory and slot (the kernel no longer touches it).
+void release_request(bch_server *s, std::map<unsigned long long, bch_server::Req>::iterator it) {
+  arena_free(s, it->second.off, it->second.bytes);
+  s->stats.bytes_in_use -= it->second.bytes;
+  s->free_slots.push_back(it->second.slot);
+  s->active.erase(it);
 }
 
 // Waits for stream `st` for at most `limit_s` seconds (no unbounded host wait on the
@@ -598,10 +607,15 @@ bch_status bch_server_poll(bch_server *s, uint64_t *done_ids, int max_ids, int *
         const unsigned long long id = c->id;
         s->comp_read++;
         auto it = s->active.find(id);
-        if (it != s->active.end()) it->second.done = true;
         s->published_open--;
-        done_ids[(*n_done)++] = id;
         s->stats.completed++;
+        if (it != s->active.end() && it->second.cancelled) {
+          // the kernel is done with a cancelled request: release it, report nothing
+          release_request(s, it);
+          continue;
+        }
+        if (it != s->active.end()) it->second.done = true;
+        done_ids[(*n_done)++] = id;
       }
       bch_status st = admit_pending(s);
       if (st == BCH_OK) st = publish_staged(s);
@@ -635,11 +649,28 @@ bch_status bch_server_fetch(bch_server *s, uint64_t id, uint64_t *hard, uint8_t 
   if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("fetch: ") + cudaGetErrorString(e));
   bch_status ws = wait_stream(s, s->cst, 30.0, "fetch copies");
   if (ws != BCH_OK) return ws;
-  arena_free(s, r.off, r.bytes);
-  s->stats.bytes_in_use -= r.bytes;
-  s->free_slots.push_back(r.slot);
-  s->active.erase(it);
+  release_request(s, it);
   return admit_pending(s);
+}
+
+bch_status bch_server_cancel(bch_server *s, uint64_t id) {
+  if (!s) return fail(BCH_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+    if (it->id == id) {  // never admitted: nothing on the device
+      s->pending.erase(it);
+      s->stats.cancelled++;
+      return BCH_OK;
+    }
+  auto it = s->active.find(id);
+  if (it == s->active.end() || it->second.cancelled) return fail(BCH_EINVAL, "unknown request");
+  s->stats.cancelled++;
+  if (it->second.done) {  // complete but not fetched
+    release_request(s, it);
+    return admit_pending(s);
+  }
+  it->second.cancelled = true;  // in flight: released when the kernel completes it
+  return BCH_OK;
 }
 
 bch_status bch_server_kernel_info(bch_server *s, char *buf, size_t capacity) {

@@ -89,9 +89,16 @@ def test_specialised_kernel_compiles_without_gpu(msg):
     assert "registers" in report
 
 
-def test_serving_kernel_compiles_without_gpu():
-    """The serving kernel specialised to a server's codes compiles for sm_103a (NVRTC,
-    no GPU): one separate copy function per code, none of them spilling for n = 63."""
+def test_serving_kernel_compiles_without_gpu(monkeypatch):
+    """The serving kernels specialised to a server's codes compile for sm_103a (NVRTC,
+    no GPU) without spilling: the block-bound kernel (the default) and the per-warp one
+    with one separate copy function per code."""
+    report = B.serve_jit_check([(63, 45), (63, 36)])
+    assert "bch_serve_blocks" in report
+    lines = report.splitlines()
+    props = lines[lines.index(next(l for l in lines if "Function properties for bch_serve_blocks" in l)) + 1]
+    assert "0 bytes spill stores" in props
+    monkeypatch.setenv("BCHDEC_SERVE_KERNEL", "warps")
     report = B.serve_jit_check([(63, 45), (63, 36)])
     assert "bch_serve_jit" in report
     assert "srv_copy_0" in report and "srv_copy_1" in report

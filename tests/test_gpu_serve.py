@@ -145,3 +145,84 @@ def test_kernel_relaunches_after_idle_exit(setup):
         assert srv.stats()["kernel_launches"] >= 2
     finally:
         srv.close()
+
+
+def test_malformed_requests_are_rejected_and_the_server_keeps_serving(setup):
+    """Host-injected malformed requests: unknown code, empty or oversized requests, a
+    row stride shorter than the code and a null buffer fail with BCH_EINVAL before any
+    device work; a valid request submitted afterwards decodes as before."""
+    import ctypes as C
+    torch, codes, stds = setup
+    srv = B.Server(codes, stds, 12, 0.78, budget_bytes=1 << 28, max_requests=16, max_frames_per_request=512)
+    try:
+        n, k = 63, 45
+        cw, llr = frames(n, k, 64, 3.0, 7100, ld=64)
+        bad = [
+            lambda: srv.submit(7, llr, 1, 0),                         # no such code
+            lambda: srv.submit(1, llr[:0], 1, 0),                     # no frames
+            lambda: srv.submit(1, np.zeros((513, 64), np.float32), 1, 0),  # above the per-request limit
+            lambda: srv.submit(1, np.ascontiguousarray(llr[:, :32]), 1, 0),  # ld < n
+        ]
+        for f in bad:
+            with pytest.raises(B.BchError) as e:
+                f()
+            assert e.value.status == B.EINVAL
+        rid = C.c_uint64()
+        rc = B.load().bch_server_submit(srv._h, 1, None, 64, 8, 1, 0, C.byref(rid))  # null llr
+        assert rc == B.EINVAL
+        assert srv.stats()["submitted"] == 0
+        good = srv.submit(1, llr, 3, 0)
+        out = _drain(srv, [good])[good]
+        ref = O.hybrid(codes[1].dense(), stds[1].dense(), llr, O.draw_autos(n, 3, 3, 0, 64), 12, 0.78)
+        tr = O.nms_enhanced(codes[1].dense(), llr, O.draw_autos(n, 3, 3, 0, 64), 12, 0.78, trace=True)
+        ok = ~ambiguous_frames(llr, tr, n)
+        assert np.array_equal(B.unpack_bits(out[0], n)[ok], ref["final"][ok])
+    finally:
+        srv.close()
+
+
+def test_cancel_queued_in_flight_and_completed_requests(setup):
+    """Cancel a request still queued for memory, one on the GPU and one completed but not
+    fetched: none of them is reported or fetchable, their memory and slots come back,
+    and the other requests' results are unchanged."""
+    import time
+    torch, codes, stds = setup
+    # a budget of about two 500-frame (127,k) requests: the rest queue
+    srv = B.Server(codes, stds, 12, 0.78, budget_bytes=600_000, max_requests=8)
+    try:
+        n, k = 127, 64
+        cw, llr = frames(n, k, 500, 2.0, 7200, ld=128)
+        rids = [srv.submit(2, llr, 1, 0) for _ in range(5)]
+        assert srv.stats()["queued"] >= 2
+        srv.cancel(rids[4])      # still queued
+        srv.cancel(rids[0])      # admitted first: on the GPU (or already done)
+        got = {}
+        for _ in range(20000):
+            for r in srv.poll(timeout_us=2000):
+                got[r] = srv.fetch(r) if r != rids[2] else None
+            if all(r in got for r in (rids[1], rids[2], rids[3])):
+                break
+        assert set(got) == {rids[1], rids[2], rids[3]}
+        srv.cancel(rids[2])      # completed, never fetched
+        for r in (rids[0], rids[2], rids[4]):
+            with pytest.raises(B.BchError):
+                srv.fetch(r)
+        with pytest.raises(B.BchError):
+            srv.cancel(rids[4])  # already cancelled
+        # the cancelled in-flight request is released once its completion is seen
+        for _ in range(200):
+            srv.poll(timeout_us=1000)
+            if srv.stats()["bytes_in_use"] == 0:
+                break
+            time.sleep(0.005)
+        st = srv.stats()
+        assert st["bytes_in_use"] == 0 and st["cancelled"] == 3 and st["in_flight"] == 0
+        assert np.array_equal(got[rids[1]][0], got[rids[3]][0])
+        ref = O.hybrid(codes[2].dense(), stds[2].dense(), llr, O.draw_autos(n, 3, 1, 0, 500), 12, 0.78,
+                       threads=None)
+        tr = O.nms_enhanced(codes[2].dense(), llr, O.draw_autos(n, 3, 1, 0, 500), 12, 0.78, trace=True,
+                            threads=None)
+        ok = ~ambiguous_frames(llr, tr, n)
+        assert np.array_equal(B.unpack_bits(got[rids[1]][0], n)[ok], ref["final"][ok])
+    finally:
+        srv.close()

@@ -130,3 +130,26 @@ def test_autograd_training_loop_on_simulated_frames(torch_cuda):
         hist.append(float(loss))
     assert np.all(np.isfinite(hist)) and torch.isfinite(alpha).all()
     assert np.mean(hist[-5:]) < np.mean(hist[:5])
+
+
+def test_training_resumes_bit_exactly(tmp_path):
+    """Six Adam steps in one call equal three steps, a save to disk and a load, and three
+    more steps that continue from the saved state: identical alpha and losses (the frames
+    of step s are frames s x batch ... of the simulated stream in both runs)."""
+    from paper_2412_20828_gb300 import build
+    build.build()
+    code = B.Code(63, 45)
+    kw = dict(n_autos=3, iters=8, steps=6, batch=4096, ebn0_lo=2.0, ebn0_hi=4.0, seed=31, lr=0.01)
+    a_full, h_full = B.train_alpha(code, kw["n_autos"], kw["iters"], 0.78, kw["steps"], kw["batch"],
+                                   kw["ebn0_lo"], kw["ebn0_hi"], kw["seed"], kw["lr"])
+    st = B.AdamState()
+    a1, h1 = B.train_alpha_resume(code, 3, 8, 0.78, st, 3, 4096, 2.0, 4.0, 31, 0.01)
+    assert st.step == 3
+    B.save_training(tmp_path / "s.npz", a1, st)
+    a1b, st2 = B.load_training(tmp_path / "s.npz")
+    a2, h2 = B.train_alpha_resume(code, 3, 8, a1b, st2, 3, 4096, 2.0, 4.0, 31, 0.01)
+    assert st2.step == 6
+    assert np.array_equal(np.concatenate([h1, h2]), h_full)
+    assert np.array_equal(a2, a_full)
+    with pytest.raises(B.BchError):  # a state of another shape is refused
+        B.train_alpha_resume(code, 3, 8, a2, st2, 1, 2048, 2.0, 4.0, 31, 0.01)
