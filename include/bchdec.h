@@ -272,9 +272,12 @@ bch_status bch_compact_failed(const uint8_t *flags, int n_frames, uint32_t *list
                               void *workspace, void *stream);
 
 /* Order-p OSD alone on the listed frames (indices into llr), overwriting their hard
- * decision; used by the hybrid decoder and exposed for testing. */
+ * decision; used by the hybrid decoder and exposed for testing.  n_frames is the number
+ * of frames in llr, hard and flags; the first min(*count, n_frames) entries of
+ * frame_list (device u32) are read and each must be < n_frames (the checked build
+ * skips and records any other). */
 bch_status bch_osd_decode(const bch_code *std_code, int order, const float *llr, int ld,
-                          const uint32_t *frame_list, const uint32_t *count, int max_frames,
+                          const uint32_t *frame_list, const uint32_t *count, int n_frames,
                           uint64_t *hard, uint8_t *flags, void *workspace, void *stream);
 
 /* Per-batch error counters (for FER/BER reporting) accumulated into
@@ -489,6 +492,39 @@ bch_status bch_train_alpha_resume(const bch_code *code, int n_autos, int iters, 
                                   bch_adam_state *state, int steps, int batch, float ebn0_lo,
                                   float ebn0_hi, uint64_t seed, float lr, float *loss_hist,
                                   void *stream);
+
+/* ---------------------------------------------------------------- checked build */
+
+/* The checked library is this library compiled with -DBCH_CHECKED
+ * (paper_2412_20828_gb300/_build/checked/libbchdec.so; the Python binding loads it when
+ * BCHDEC_CHECKED=1).  Its kernels validate every index they take from caller-supplied
+ * device data before using it:
+ *   - each packed automorphism s | j << 8 (Sec. III-B: pi(i) = 2^j i + s mod n) must
+ *     have s < n and j < m, n = 2^m - 1 (enhanced NMS in every kernel variant, the
+ *     hybrid, no-allocation and training entry points, the backward pass);
+ *   - each OSD frame-list entry (bch_osd_decode) must be < n_frames.
+ * An invalid value never traps: it is replaced by a harmless one (the identity
+ * automorphism, so the frame is decoded as if that copy were unpermuted; a bad list
+ * entry is skipped) and recorded in the current device's check word:
+ *   word[0]  OR of BCH_CHECK_* bits,
+ *   word[1]  number of invalid values met (a value read by several threads counts once
+ *            per reader),
+ *   word[2]  smallest frame index holding an invalid automorphism (0xffffffff: none),
+ *   word[3]  smallest OSD list position holding an invalid entry (0xffffffff: none).
+ * Automorphisms the library draws itself (host pipeline, server, simulation) are valid
+ * by construction.  The ordinary build does the same work without the checks and
+ * takes such values as given (results undefined for invalid ones).  No counterpart in
+ * the paper: a debugging aid. */
+#define BCH_CHECK_AUTOMORPHISM 1u
+#define BCH_CHECK_OSD_FRAME 2u
+
+/* 1 in the checked build, else 0. */
+int bch_is_checked(void);
+
+/* Synchronises `stream`, copies the current device's check word to word_out (host
+ * u32 [4]) and, when clear != 0, resets it (0, 0, 0xffffffff, 0xffffffff).
+ * BCH_EINVAL in the ordinary build or for a null word_out. */
+bch_status bch_check_read(uint32_t *word_out, int clear, void *stream);
 
 /* ---------------------------------------------------------------- misc */
 

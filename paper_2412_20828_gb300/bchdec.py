@@ -3,7 +3,9 @@
 Argument marshalling only: every step of decoding runs in the CUDA library.  Device
 buffers are torch CUDA tensors (torch is used for memory and streams); the calls are
 asynchronous on the current torch stream unless ``stream`` is given.  Loading fails
-loudly when ``libbchdec.so`` has not been built -- there is no CPU fallback.
+loudly when ``libbchdec.so`` has not been built -- there is no CPU fallback.  With
+BCHDEC_CHECKED=1 in the environment the checked build (``_build/checked``, compiled
+with -DBCH_CHECKED) is loaded instead.
 """
 from __future__ import annotations
 
@@ -15,6 +17,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libbchdec.so")
+LIB_PATH_CHECKED = os.path.join(_HERE, "_build", "checked", "libbchdec.so")
+CHECK_AUTOMORPHISM, CHECK_OSD_FRAME = 1, 2
 
 OK, EINVAL, ENOMEM, ECUDA, ERANK, ETIMEOUT, EBUDGET, EBUSY = range(8)
 PCM_STANDARD, PCM_OPTIMIZED = 0, 1
@@ -34,6 +38,7 @@ EXPORTS = (
     "bch_server_create", "bch_server_submit", "bch_server_poll", "bch_server_fetch",
     "bch_server_get_stats", "bch_server_cancel", "bch_server_kernel_info", "bch_serve_jit_check", "bch_server_destroy",
     "bch_serve_bench",
+    "bch_is_checked", "bch_check_read",
     "bch_status_str", "bch_last_error", "bch_version",
 )
 
@@ -97,11 +102,12 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(LIB_PATH):
+        path = LIB_PATH_CHECKED if os.environ.get("BCHDEC_CHECKED") == "1" else LIB_PATH
+        if not os.path.exists(path):
             raise RuntimeError(
-                f"{LIB_PATH} is missing: build it with "
+                f"{path} is missing: build it with "
                 "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
-        lib = C.CDLL(LIB_PATH)
+        lib = C.CDLL(path)
         P, i, u64, f, sz = C.c_void_p, C.c_int, C.c_uint64, C.c_float, C.c_size_t
         st = C.c_int
         sig = {
@@ -149,6 +155,8 @@ def load():
             "bch_serve_jit_check": (st, [i, C.POINTER(C.c_int), C.POINTER(C.c_int), u64, C.c_char_p, sz]),
             "bch_server_destroy": (None, [P]),
             "bch_serve_bench": (st, [P, C.POINTER(ServeBenchConfig), C.POINTER(ServeBenchResult)]),
+            "bch_is_checked": (i, []),
+            "bch_check_read": (st, [P, i, P]),
             "bch_status_str": (C.c_char_p, [i]),
             "bch_last_error": (C.c_char_p, []),
             "bch_version": (C.c_char_p, []),
@@ -399,11 +407,13 @@ def hybrid_decode_noalloc(code: Code, std_code: Code, p: NmsParams, llr, autos, 
 
 def osd_decode(std_code: Code, order, llr, frame_list, count, hard, flags=None, ws=None,
                stream=None):
+    """Order-p OSD on the first min(count, len(llr)) frames listed in frame_list (device
+    u32 indices into llr, each < len(llr))."""
     import torch
     F, ld = llr.shape
     ws = ws if ws is not None else torch.zeros(256, dtype=torch.uint8, device=llr.device)
     _check(load().bch_osd_decode(std_code.handle, order, _ptr(llr), ld, _ptr(frame_list),
-                                 _ptr(count), frame_list.shape[0], _ptr(hard), _ptr(flags),
+                                 _ptr(count), F, _ptr(hard), _ptr(flags),
                                  _ptr(ws), _stream(stream)), "bch_osd_decode")
 
 
@@ -499,6 +509,20 @@ class DecoderTiming(C.Structure):
     _fields_ = [("calls", C.c_longlong), ("chunks", C.c_longlong), ("in_place_chunks", C.c_longlong),
                 ("ms_wall", C.c_double),
                 ("ms_h2d", C.c_double), ("ms_decode", C.c_double), ("ms_d2h", C.c_double)]
+
+
+def is_checked() -> bool:
+    """True when the loaded library is the checked build (-DBCH_CHECKED)."""
+    return bool(load().bch_is_checked())
+
+
+def check_read(clear=True, stream=None) -> np.ndarray:
+    """The checked build's device check word (u32 [4]: CHECK_* bits, number of invalid
+    values, smallest frame with an invalid automorphism, smallest OSD list position with
+    an invalid entry; 0xffffffff where none); synchronises the stream."""
+    w = np.zeros(4, np.uint32)
+    _check(load().bch_check_read(w.ctypes.data, 1 if clear else 0, _stream(stream)), "bch_check_read")
+    return w
 
 
 def kernel_launches() -> int:

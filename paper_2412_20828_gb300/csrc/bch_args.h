@@ -21,6 +21,7 @@ struct OsdArgs {
   uint8_t *flags;
   unsigned *queue;
   int scale_input;  // 1: scale each frame's input by the power of two putting max |L| in [2^15, 2^16)
+  unsigned *check;  // checked builds: the device's check word [4]; else unused
 };
 
 struct GenArgs {
@@ -42,6 +43,7 @@ struct BwdArgs {
   const float *grad_out;
   float *grad_llr;
   float *partial;  // [blocks][I]
+  unsigned *check;  // checked builds: the device's check word [4]; else unused
   float alpha[32];
 };
 
@@ -60,6 +62,10 @@ size_t anneal_smem_bytes(int Mo);
 // current device; raises the kernel's shared-memory limit when this launch needs more
 // than any before.  Remembered per combination, so repeated launches cost no driver
 // queries.
+// Checked builds: the current device's check word (u32 [4]); nullptr otherwise or if the
+// symbol cannot be resolved.
+unsigned *check_word();
+
 cudaError_t launch_geometry(const void *fn, int tpb, size_t smem, int *sms, int *per_sm);
 cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st);
 cudaError_t launch_osd(const OsdArgs &a, cudaStream_t st);

@@ -12,6 +12,9 @@ constexpr int kMaxGroups = 16;
 constexpr int kMaxN = 127;
 constexpr unsigned kFlagConverged = 1u;
 constexpr unsigned kFlagOsd = 2u;
+// Checked builds (BCH_CHECKED): bits of the check word's first entry.
+constexpr unsigned kCheckAutomorphism = 1u;
+constexpr unsigned kCheckOsdFrame = 2u;
 
 // Layout of a code object on the device.  Rows are grouped by weight; each group
 // stores its rows' column codes d(u) = u | u << m (so that the Frobenius power j of u,
@@ -42,6 +45,7 @@ struct NmsArgs {
   float *llr_out;
   float *ckpt;  // training checkpoints [I+1][F][ld] or null
   unsigned *queue;
+  unsigned *check;  // checked builds: the device's check word [4]; else unused
   int I, early_stop, msg, rescale;
   float alpha[32];
 };

@@ -57,6 +57,25 @@ bch_status fail(bch_status s, const std::string &msg) {
 }  // namespace bchlib
 
 namespace bchlib {
+#ifdef BCH_CHECKED
+// The checked build's check word: flags, count of invalid values, smallest frame with an
+// invalid automorphism, smallest OSD list position with an invalid entry.
+__device__ unsigned g_check_word[4] = {0u, 0u, 0xffffffffu, 0xffffffffu};
+#endif
+
+unsigned *check_word() {
+#ifdef BCH_CHECKED
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_check_word) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<unsigned *>(p);
+#else
+  return nullptr;
+#endif
+}
+
 cudaError_t launch_geometry(const void *fn, int tpb, size_t smem, int *sms, int *per_sm) {
   // The shared-memory limit is one attribute per function (per device): it holds the
   // last value set, so it is raised to the largest size any launch has needed and never
@@ -303,6 +322,7 @@ NmsArgs make_nms_args(const bch_code *code, const bch_nms_params *p, const float
   a.llr_out = llr_out;
   a.ckpt = nullptr;
   a.queue = queue;
+  a.check = check_word();
   a.I = p->iters;
   a.early_stop = p->early_stop ? 1 : 0;
   a.msg = int(p->msg);
@@ -334,6 +354,34 @@ const char *bch_last_error(void) { return g_last_error.c_str(); }
 const char *bch_version(void) { return "bchdec-gb300 1.0 (sm_103a)"; }
 
 unsigned long long bch_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int bch_is_checked(void) {
+#ifdef BCH_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+bch_status bch_check_read(uint32_t *word_out, int clear, void *stream) {
+#ifdef BCH_CHECKED
+  if (!word_out) return fail(BCH_EINVAL, "null word_out");
+  unsigned *w = check_word();
+  if (!w) return fail(BCH_ECUDA, "the check word's device address");
+  BCH_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "synchronise the stream");
+  BCH_CUDA(cudaMemcpy(word_out, w, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost), "read the check word");
+  if (clear) {
+    const unsigned init[4] = {0u, 0u, 0xffffffffu, 0xffffffffu};
+    BCH_CUDA(cudaMemcpy(w, init, sizeof(init), cudaMemcpyHostToDevice), "clear the check word");
+  }
+  return BCH_OK;
+#else
+  (void)word_out;
+  (void)clear;
+  (void)stream;
+  return fail(BCH_EINVAL, "this library was built without BCH_CHECKED");
+#endif
+}
 
 static HoOptions ho_options(const bch_pcm_opts *opts) {
   HoOptions o;
@@ -713,12 +761,13 @@ static bch_status run_osd(const bch_code *std_code, int order, const float *llr,
   a.flags = flags;
   a.queue = queue;
   a.scale_input = scale_input;
+  a.check = check_word();
   BCH_CUDA(launch_osd(a, st), "osd kernel");
   return BCH_OK;
 }
 
 bch_status bch_osd_decode(const bch_code *std_code, int order, const float *llr, int ld,
-                          const uint32_t *frame_list, const uint32_t *count, int max_frames,
+                          const uint32_t *frame_list, const uint32_t *count, int n_frames,
                           uint64_t *hard, uint8_t *flags, void *workspace, void *stream) {
   if (!frame_list || !count || !hard || !llr) return fail(BCH_EINVAL, "null argument");
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
@@ -727,7 +776,7 @@ bch_status bch_osd_decode(const bch_code *std_code, int order, const float *llr,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned *queue = reinterpret_cast<unsigned *>(workspace);
   BCH_CUDA(cudaMemsetAsync(queue, 0, 16, st), "clear queue");
-  return run_osd(std_code, order, llr, ld, frame_list, count, max_frames, hard, flags, queue + 1, st);
+  return run_osd(std_code, order, llr, ld, frame_list, count, n_frames, hard, flags, queue + 1, st);
 }
 
 bch_status bch_hybrid_decode(const bch_code *code, const bch_code *std_code, const bch_nms_params *params,
@@ -816,6 +865,7 @@ bch_status bch_nms_backward(const bch_code *code, const bch_nms_params *params, 
   a.grad_out = grad_out;
   a.grad_llr = grad_llr;
   a.partial = reinterpret_cast<float *>(static_cast<unsigned char *>(workspace) + L.red);
+  a.check = check_word();
   for (int t = 0; t < 32; t++) a.alpha[t] = t < params->iters ? params->alpha[t] : 0.0f;
   BCH_CUDA(launch_backward(a, grad_alpha, static_cast<cudaStream_t>(stream)), "backward");
   return BCH_OK;

@@ -625,9 +625,21 @@ cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
   return k;
 }
 
+// The library's own build defines, prepended to every run-time source: checked builds
+// compile the specialised kernels with the same index checks as the precompiled ones
+// (and, the define being part of the text, cache them apart).
+static std::string with_build_defines(const std::string &src) {
+#ifdef BCH_CHECKED
+  return "#define BCH_CHECKED 1\n" + src;
+#else
+  return src;
+#endif
+}
+
 // Compiles `src` (or loads it from the on-disk cache) and returns its kernel `entry`;
 // cached in the process per source text.  On failure returns nullptr and sets *err.
-static cudaKernel_t compile_source(const std::string &src, const char *entry, std::string *err) {
+static cudaKernel_t compile_source(const std::string &src_in, const char *entry, std::string *err) {
+  const std::string src = with_build_defines(src_in);
   std::shared_ptr<Compiled> cp;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -717,7 +729,8 @@ bool jit_serve_compile_check(const bch_code *const *codes, int n_codes, std::str
   return compile_check_source(jit_serve_source(codes, n_codes), "bch_serve_jit", log);
 }
 
-static bool compile_check_source(const std::string &src, const char *entry, std::string *log) {
+static bool compile_check_source(const std::string &src_in, const char *entry, std::string *log) {
+  const std::string src = with_build_defines(src_in);
   NvrtcApi &api = nvrtc();
   if (!api.ok) {
     *log = api.err;

@@ -33,6 +33,17 @@ __global__ void __launch_bounds__(32 * kOsdWarps) osd_kernel(const OsdArgs a) {
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
     const int f = int(a.list[item]);
+#ifdef BCH_CHECKED
+    // a list entry outside the frames is recorded and skipped (item is warp-uniform)
+    if (uint32_t(f) >= uint32_t(a.max_frames)) {
+      if (lane == 0 && a.check) {
+        atomicOr(a.check, kCheckOsdFrame);
+        atomicAdd(a.check + 1, 1u);
+        atomicMin(a.check + 3, item);
+      }
+      continue;
+    }
+#endif
     const float *L = a.llr + size_t(f) * a.ld;
     const int sexp = a.scale_input ? osd_input_exponent(L, a.n) : 0;
     osd_one_frame(S, a.n, a.k, a.M, a.cols, L, a.order, a.hard + size_t(f) * W64,

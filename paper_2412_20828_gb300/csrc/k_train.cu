@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(TPB) nms_backward_kernel(const BwdArgs a) {
 #pragma unroll
     for (int p = 0; p < 9; p++) {
       if (p < a.P) {
-        const uint32_t v = a.autos[size_t(f) * a.P + p];
+        const uint32_t v = checked_auto(a.autos[size_t(f) * a.P + p], uint32_t(n), uint32_t(m), a.check, f);
         const uint32_t s = v & 0xffu, j = v >> 8;
         const uint32_t rs = j ? (((s >> j) | (s << (m - j))) & uint32_t(n)) : s;
         const uint32_t spv = rs ? uint32_t(n) - rs : 0u;

@@ -36,6 +36,25 @@ __device__ __forceinline__ uint32_t bfe32(uint32_t x, uint32_t pos, uint32_t len
   return r;
 }
 
+// A packed automorphism s | j << 8 of frame f as the kernels take it.  Checked builds
+// accept only the group's elements (s < n, j < m: pi(i) = 2^j i + s mod n, Sec. III-B)
+// and replace any other value by the identity after recording it in the check word
+// (flag, count, smallest frame), so that no index derived from it leaves [0, n).
+__device__ __forceinline__ uint32_t checked_auto(uint32_t v, uint32_t n, uint32_t m,
+                                                 unsigned *check, int f) {
+#ifdef BCH_CHECKED
+  if ((v & 0xffu) >= n || (v >> 8) >= m) {
+    if (check) {
+      atomicOr(check, kCheckAutomorphism);
+      atomicAdd(check + 1, 1u);
+      atomicMin(check + 2, unsigned(f));
+    }
+    return 0u;
+  }
+#endif
+  return v;
+}
+
 // (a + b) mod n for a, b in [0, n): min(a + b, a + b - n) in unsigned arithmetic.
 __device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, uint32_t n) {
   uint32_t x = a + b;
@@ -410,7 +429,7 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
           }
         }
         for (int p = 0; p < a.P; p++) {
-          const uint32_t v = a.autos[size_t(f) * a.P + p];
+          const uint32_t v = checked_auto(a.autos[size_t(f) * a.P + p], uint32_t(n), uint32_t(m), a.check, f);
           const uint32_t s = v & 0xffu, j = v >> 8;
           // pi^-1(u) = rotr_m(u, j) + s' with s' = -rotr_m(s, j) mod n
           const uint32_t rs = j ? (((s >> j) | (s << (m - j))) & uint32_t(n)) : s;
@@ -631,7 +650,7 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
           }
         }
         for (int p = 0; p < a.P; p++) {
-          const uint32_t v = a.autos[size_t(f) * a.P + p];
+          const uint32_t v = checked_auto(a.autos[size_t(f) * a.P + p], uint32_t(n), uint32_t(m), a.check, f);
           const uint32_t sh = v & 0xffu, j = v >> 8;
           const uint32_t rs = j ? (((sh >> j) | (sh << (m - j))) & uint32_t(n)) : sh;
           ctx[p * Fs] = j | ((rs ? uint32_t(n) - rs : 0u) << 8);

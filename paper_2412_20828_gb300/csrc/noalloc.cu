@@ -128,6 +128,7 @@ extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_
   a.flags = flags;
   a.llr_out = llr_out;
   a.queue = queue;
+  a.check = check_word();
   a.I = p->iters;
   a.early_stop = p->early_stop ? 1 : 0;
   a.msg = int(p->msg);
@@ -155,6 +156,7 @@ extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_
   o.list = list;
   o.count = count;
   o.max_frames = n_frames;
+  o.check = check_word();
   o.order = p->osd_order;
   o.hard = hard;
   o.flags = flags;

@@ -28,6 +28,31 @@ def test_exports_every_declared_symbol(lib):
         assert getattr(lib, name) is not None
 
 
+def test_checked_build_is_separate_and_exports_every_symbol(lib):
+    """The ordinary library reports no checks and refuses to read a check word (before
+    any CUDA call); the checked one (-DBCH_CHECKED, loaded in a child process) exports
+    the same symbols and reports its checks."""
+    import ctypes as C
+    import subprocess
+    import sys
+    import numpy as np
+    assert lib.bch_is_checked() == 0
+    w = np.zeros(4, np.uint32)
+    assert lib.bch_check_read(w.ctypes.data, 1, None) == B.EINVAL
+    assert b"BCH_CHECKED" in lib.bch_last_error()
+    from paper_2412_20828_gb300 import build
+    path = build.build(checked=True)
+    assert path == B.LIB_PATH_CHECKED
+    code = ("import ctypes, sys\n"
+            f"lib = ctypes.CDLL({path!r})\n"
+            f"names = {list(B.EXPORTS)!r}\n"
+            "assert all(getattr(lib, n) is not None for n in names)\n"
+            "print(lib.bch_is_checked())\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "1"
+
+
 def test_status_strings(lib):
     assert lib.bch_status_str(0) == b"ok"
     assert lib.bch_status_str(4).startswith(b"rank")
