@@ -104,6 +104,9 @@ const char *row_macros(int msg) {
 #define BCH_R2F(u) BCH_R2(u)
 #define BCH_RE }
 #define BCH_FIN(u) ((z[u] < 0) ? -BCH_SV(u) : BCH_SV(u))
+#define BCH_R0B int n1_ = 1 << 20, n2_ = 1 << 20;
+#define BCH_R1B(u) { const int a_ = abs(z[u]); n2_ = min(n2_, max(n1_, a_)); n1_ = min(n1_, a_); }
+#define BCH_RJ m2_ = __vimin3_s32(max(m1_, n1_), m2_, n2_); m1_ = min(m1_, n1_);
 )";
   if (msg == 1)
     return R"(
@@ -122,6 +125,9 @@ const char *row_macros(int msg) {
   BCH_SV(u) = __fmaf_rn(dv_, __saturatef(__fmaf_rn(-p_, 0x1p100f, 1.0f)), BCH_SV(u) + v1_); }
 #define BCH_RE }
 #define BCH_FIN(u) flip_sign(BCH_SV(u), __float_as_uint(z[u]))
+#define BCH_R0B float n1_ = FLT_MAX, n2_ = FLT_MAX;
+#define BCH_R1B(u) n2_ = fminf(n2_, fmaxf(n1_, fabsf(z[u]))); n1_ = fminf(n1_, fabsf(z[u]));
+#define BCH_RJ m2_ = bch_min3f(fmaxf(m1_, n1_), m2_, n2_); m1_ = fminf(m1_, n1_);
 )";
   return R"(
 #define BCH_VT float
@@ -138,6 +144,9 @@ const char *row_macros(int msg) {
   BCH_SV(u) = __fmaf_rn(dv_, __saturatef(__fmaf_rn(-p_, 0x1p100f, 1.0f)), BCH_SV(u) + v1_); }
 #define BCH_RE }
 #define BCH_FIN(u) flip_sign(BCH_SV(u), __float_as_uint(z[u]))
+#define BCH_R0B float n1_ = FLT_MAX, n2_ = FLT_MAX;
+#define BCH_R1B(u) n2_ = fminf(n2_, fmaxf(n1_, fabsf(z[u]))); n1_ = fminf(n1_, fabsf(z[u]));
+#define BCH_RJ m2_ = bch_min3f(fmaxf(m1_, n1_), m2_, n2_); m1_ = fminf(m1_, n1_);
 )";
 }
 
@@ -207,6 +216,11 @@ int jit_block_size(int n) {
 // BCHDEC_JIT_PAIRS=1 tracks min1/min2 two edges at a time (tuning knob; off by default:
 // it needs more registers and measured 1-2% slower).
 bool jit_pairs() { return env_int("BCHDEC_JIT_PAIRS", 0, 1, 0) == 1; }
+// BCHDEC_JIT_CHAINS=2 runs each row's first pass as two independent min1/min2 chains
+// (even and odd edges) joined at the end -- min1 = min(a1, b1), min2 = min(max(a1, b1),
+// a2, b2), the row's two smallest magnitudes whatever the order, so the results are
+// bit-identical -- giving the scheduler two dependency chains per row (tuning knob).
+int jit_chains() { return env_int("BCHDEC_JIT_CHAINS", 1, 2, 1); }
 // Percentage of output-pass edges emitted in the compare-free form: with t = |z| - min1
 // (>= 0), g = sat(1 - (t 2^100) 2^100) is exactly 1 when t = 0 and 0 otherwise
 // (denormals included: t >= 2^-149), and fma(dv, g, S + v1) rounds like the
@@ -292,7 +306,13 @@ static void emit_copy_body(std::ostringstream &o, const bch_code *c, int msg, in
     o << "    BCH_R0";
     size_t e = 0;
     const bool pairs = jit_pairs();
-    if (pairs && cols.size() >= 2) {
+    if (jit_chains() == 2 && cols.size() >= 4) {
+      o << " BCH_R0B";
+      for (size_t q = 0; q < cols.size(); q++) o << (q & 1 ? " BCH_R1B(" : " BCH_R1(") << cols[q] << ")";
+      o << " BCH_RJ";
+      e = cols.size();
+    }
+    if (pairs && e == 0 && cols.size() >= 2) {
       o << " BCH_R1F(" << cols[0] << ", " << cols[1] << ")";
       e = 2;
     }
@@ -599,7 +619,8 @@ cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err
 // The tuning knobs that shape the generated source (read from the environment).
 static std::string jit_knob_signature(int n) {
   char buf[96];
-  std::snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d", jit_block_size(n), jit_min_blocks(n), int(jit_pairs()),
+  std::snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d", jit_block_size(n), jit_min_blocks(n),
+                int(jit_pairs()) + 2 * jit_chains(),
                 jit_fma_percent(), env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, 0), jit_scratch_words(n),
                 int(jit_split(n)));
   return buf;
