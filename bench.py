@@ -614,6 +614,14 @@ def main():
     roofline = nms_roofline(B, torch, dev, clocks, edge_updates, nms_time, kinfo, F, 63,
                             JIT_DRAM_BYTES_PER_FRAME if msg == B.MSG_FP32 else None)
 
+    # the step's decisions on the oracle's sample (frames 0..N-1 of every point), taken
+    # now: the legs below decode other message formats into the same buffers
+    gpu_on_sample = {}
+    for st in states:
+        for pi, e in enumerate(POINTS):
+            sl = slice(pi * Bp, pi * Bp + min(args.cpu_frames_per_point, Bp))
+            gpu_on_sample[(st["n"], st["k"], e)] = int((st["hard"][sl] != st["cw"][sl]).any(dim=1).sum())
+
     # ---- the same step with reduced-precision message storage (throughput only)
     msg_legs = {}
     for name in [x for x in args.msg_legs.split(",") if x and x != args.msg]:
@@ -770,12 +778,6 @@ def main():
         outside95 = 0
         a_fw = 0.05 / max(1, len(per_point))
         N = args.cpu_frames_per_point
-        gpu_on_sample = {}
-        for st in states:
-            for pi, e in enumerate(POINTS):
-                sl = slice(pi * Bp, pi * Bp + min(N, Bp))
-                err = (st["hard"][sl] != st["cw"][sl]).any(dim=1)
-                gpu_on_sample[(st["n"], st["k"], e)] = int(err.sum())
         for pp in per_point:
             n, k = map(int, pp["code"].strip("()").split(","))
             fe, nn = res[(n, k, pp["ebn0"])]

@@ -554,7 +554,12 @@ bch_status bch_server_create(const bch_server_config *cfg, bch_server **out) {
     return fail(BCH_ECUDA, "serve kernel attributes");
   }
   s->blocks = s->threads > 32 ? sms : (cfg->warps > 0 ? cfg->warps : sms * per_sm);
-  cudaDeviceSynchronize();
+  // the set-up copies and clears above ran on the legacy stream: wait for those alone,
+  // not for the device (another server's persistent kernel may be resident and busy)
+  if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
+    cleanup();
+    return fail(BCH_ECUDA, "server set-up copies");
+  }
   *out = s;
   return BCH_OK;
 }
@@ -829,16 +834,37 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
     p.early_stop = 1;
     p.msg = BCH_MSG_FP32;
     p.osd_order = c->osd_order;
+    // stream-ordered allocations: unlike cudaFree, cudaFreeAsync does not wait for the
+    // whole device, where a server's persistent kernel may still be resident
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    auto release = [&]() {
+      auto drop = [&](void *q) {
+        if (q) cudaFreeAsync(q, st);
+      };
+      for (int k = 0; k < nc; k++) {
+        drop(dllr[k]);
+        drop(daut[k]);
+        drop(dhard[k]);
+        drop(dit[k]);
+        drop(dfl[k]);
+        drop(dws[k]);
+      }
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    };
     for (int k = 0; k < nc; k++) {
       size_t wsb = 0;
       bch_workspace_size(c->codes[k], &p, cap, &wsb);
-      if (cudaMalloc(&dllr[k], size_t(cap) * c->lds[k] * 4) != cudaSuccess ||
-          cudaMalloc(&daut[k], size_t(cap) * p.n_autos * 2) != cudaSuccess ||
-          cudaMalloc(&dhard[k], size_t(cap) * 16) != cudaSuccess || cudaMalloc(&dit[k], cap) != cudaSuccess ||
-          cudaMalloc(&dfl[k], cap) != cudaSuccess || cudaMalloc(&dws[k], wsb) != cudaSuccess)
+      if (cudaMallocAsync(reinterpret_cast<void **>(&dllr[k]), size_t(cap) * c->lds[k] * 4, st) != cudaSuccess ||
+          cudaMallocAsync(reinterpret_cast<void **>(&daut[k]), size_t(cap) * p.n_autos * 2, st) != cudaSuccess ||
+          cudaMallocAsync(reinterpret_cast<void **>(&dhard[k]), size_t(cap) * 16, st) != cudaSuccess ||
+          cudaMallocAsync(reinterpret_cast<void **>(&dit[k]), cap, st) != cudaSuccess ||
+          cudaMallocAsync(reinterpret_cast<void **>(&dfl[k]), cap, st) != cudaSuccess ||
+          cudaMallocAsync(&dws[k], wsb, st) != cudaSuccess) {
+        release();
         return fail(BCH_ENOMEM, "static batching buffers");
+      }
     }
     size_t next = 0;
     bch_status sfail = BCH_OK;
@@ -909,15 +935,7 @@ bch_status bch_serve_bench(bch_server *srv, const bch_serve_bench_config *c, bch
       next = end;
     }
     cudaStreamSynchronize(st);
-    for (int k = 0; k < nc; k++) {
-      cudaFree(dllr[k]);
-      cudaFree(daut[k]);
-      cudaFree(dhard[k]);
-      cudaFree(dit[k]);
-      cudaFree(dfl[k]);
-      cudaFree(dws[k]);
-    }
-    cudaStreamDestroy(st);
+    release();
     if (sfail != BCH_OK) return sfail;
   }
   const double el = now_s();
