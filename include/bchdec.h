@@ -87,6 +87,17 @@ typedef struct {
                           not depend on a common scale -- so that its integer weights
                           floor(|y| 2^24) resolve the values; needs llr_out, which
                           receives y and which the OSD reads                             */
+  int qfrac;           /* 8-bit form only (msg = INT8, n_autos >= 1), 0..8: fractional
+                          bits kept in the check-to-variable magnitudes.  0: c2v =
+                          rne(alpha min_q) in units of the stored LSB (1/4).  f > 0: c2v =
+                          rne(alpha min_q 2^f) in units of 2^-f LSB, summed exactly, and
+                          the merge stores clamp(rne(N / D), +-31) of the exact quotient,
+                          N = P 2^f q + sum, D = P 2^f (2^k more after k rescale
+                          halvings); y keeps its 8-bit storage.  With rescale = 1 the
+                          input is also quantised after the power of two 2^-k0 that keeps
+                          max |4x| <= 31 (k0 starts the frame's exponent), so strong
+                          inputs are not clipped.  Needs 0 <= alpha_t <= 4 (the sums stay
+                          exact in FP32).  Zero-initialise the struct to leave it 0       */
 } bch_nms_params;
 
 /* Per-frame flag bits written by the decoders. */

@@ -73,7 +73,7 @@ def _load():
             "or_nms_enhanced_f32": (i, [P, i, i, P, i, i, i, P, i, P, i, P, P, P, P]),
             "or_osd": (i, [P, i, i, P, i, i, i, P, P, P]),
             "or_q16": (d, [d]),
-            "or_nms_enhanced_q": (i, [P, i, i, P, i, i, i, P, i, P, i, i, i, P, P, P, P, P]),
+            "or_nms_enhanced_q": (i, [P, i, i, P, i, i, i, P, i, P, i, i, i, i, P, P, P, P, P]),
             "or_ml": (i, [i, i, P, i, i, P]),
             "or_nms_train_grad": (i, [P, i, i, P, i, i, i, P, i, P, P, P, P, P, P, P]),
         }
@@ -338,8 +338,11 @@ def q16(x: float) -> float:
     return _load().or_q16(float(x))
 
 
-def nms_enhanced_q(Ho, llr, autos, iters, alpha, fmt, rescale=False, early_stop=True, threads=1):
-    """Algorithm 1 with FP16 (fmt=1) or 8-bit (fmt=2) storage; see the C header."""
+def nms_enhanced_q(Ho, llr, autos, iters, alpha, fmt, rescale=False, early_stop=True, threads=1,
+                   qfrac=0):
+    """Algorithm 1 with FP16 (fmt=1) or 8-bit (fmt=2) storage; with qfrac > 0 (8-bit only)
+    the check-to-variable magnitudes keep qfrac fractional bits and the merge rounds the
+    exact quotient; see the C file."""
     Ho = np.ascontiguousarray(Ho, np.uint8)
     M, n = Ho.shape
     llr = np.ascontiguousarray(llr, np.float32)
@@ -356,7 +359,7 @@ def nms_enhanced_q(Ho, llr, autos, iters, alpha, fmt, rescale=False, early_stop=
 
     def run(a, b):
         _check(lib.or_nms_enhanced_q(_p(Ho), M, n, _p(llr[a:]), ld, b - a, P, _p(autos[a:]), iters,
-                                     _p(al), int(early_stop), fmt, int(rescale), _p(hard[a:]),
+                                     _p(al), int(early_stop), fmt, int(rescale), int(qfrac), _p(hard[a:]),
                                      _p(it[a:]), _p(conv[a:]), _p(y[a:]), _p(margin[a:])),
                "nms_enhanced_q")
 

@@ -39,7 +39,10 @@
  *                                     FP64 decoder's on unambiguous frames.
  *   or_nms_enhanced_q, or_q16         pinned: binary16 rounding against numpy's
  *                                     float16; quantised decode equals the FP64 decode
- *                                     on inputs that are exact in the format.
+ *                                     on inputs that are exact in the format; hand-
+ *                                     derived examples of every rounding, saturation and
+ *                                     rescale branch, with and without fractional c2v
+ *                                     bits (qfrac).
  *   or_philox4x32_10                  pinned: published known-answer vectors.
  *   or_splitmix64                     pinned: published first output.
  */
@@ -1222,11 +1225,23 @@ static double q16_spacing(double x) {
   return q;
 }
 
+/* Round-half-even of num / den (den > 0), exact in 64-bit integers. */
+static int64_t rne_div(int64_t num, int64_t den) {
+  int64_t q = num / den, r = num % den;
+  if (r < 0) {
+    r += den;
+    q -= 1;
+  }
+  if (2 * r > den || (2 * r == den && (q & 1))) q += 1;
+  return q;
+}
+
 int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld, int F, int P,
                       const uint16_t *autos, int iters, const double *alpha, int early_stop,
-                      int fmt, int rescale, uint8_t *hard, int *iters_used, uint8_t *converged,
-                      double *y_out, double *margin) {
+                      int fmt, int rescale, int qfrac, uint8_t *hard, int *iters_used,
+                      uint8_t *converged, double *y_out, double *margin) {
   if (fmt != 1 && fmt != 2) return OR_EARG;
+  if (qfrac < 0 || qfrac > 8 || (qfrac > 0 && fmt != 2)) return OR_EARG;
   double y[128], yn[128], z[128], S[128], Sa[128], sum[128], suma[128], rowbuf[128];
   double Sq[128], qmin[128];
   int vars[128], pi[128];
@@ -1237,9 +1252,19 @@ int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld,
     const uint16_t *aut = autos + (size_t)f * P;
     int escale = 0;
     double mar = INFINITY;
+    /* with fractional bits and the rescale, the 8-bit input is quantised after the power
+     * of two 2^-k0 that keeps max |4x| <= 31 (k0 starts the frame's exponent) */
+    int k0 = 0;
+    if (fmt == 2 && rescale && qfrac > 0) {
+      double mx4 = 0.0;
+      for (int i = 0; i < n; i++)
+        if (fabs(4.0 * (double)L[i]) > mx4) mx4 = fabs(4.0 * (double)L[i]);
+      while (mx4 > ldexp(31.0, k0) && k0 < 60) k0++;
+    }
+    escale = k0;
     for (int i = 0; i < n; i++) {
       double x = (double)L[i];
-      y[i] = fmt == 1 ? or_q16(x) : q8(4.0 * x);
+      y[i] = fmt == 1 ? or_q16(x) : q8(ldexp(4.0 * x, -k0));
       c[i] = x < 0.0;
     }
     int t_run = 0, ok = 0;
@@ -1267,7 +1292,9 @@ int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld,
               if (fabs(rowbuf[e2]) < mn) mn = fabs(rowbuf[e2]);
             }
             double mag = alpha[t - 1] * mn;
-            mag = fmt == 1 ? or_q16(mag) : rint(mag);
+            /* 8-bit form: rne(alpha min) in units of the stored LSB, or with qfrac
+             * fractional bits rne(alpha min 2^qfrac) (exact products in FP64) */
+            mag = fmt == 1 ? or_q16(mag) : rint(ldexp(mag, qfrac));
             S[vars[e]] += sg * mag;
             Sa[vars[e]] += mag + v1;
             if (mag != 0.0 && q16_spacing(mag) < Sq[vars[e]]) Sq[vars[e]] = q16_spacing(mag);
@@ -1279,6 +1306,32 @@ int or_nms_enhanced_q(const uint8_t *Ho, int M, int n, const float *llr, int ld,
           suma[i] += Sa[pi[i]];
           if (Sq[pi[i]] < qmin[i]) qmin[i] = Sq[pi[i]];
         }
+      }
+      if (qfrac > 0) {
+        /* 8-bit storage, c2v sums in units of 2^-qfrac LSB: the merged value is the
+         * rational N / D with N = P 2^qfrac q + sum (an exact integer) and D = P
+         * 2^qfrac; its sign is the hard decision, the optional rescale halves while
+         * max |N| / D > 31, and the stored value is clamp(rne(N / (D 2^k)), +-31). */
+        const double D = ldexp((double)P, qfrac);
+        double mxN = 0.0;
+        for (int i = 0; i < n; i++) {
+          yn[i] = y[i] * D + sum[i];
+          c[i] = yn[i] < 0.0;
+          if (fabs(yn[i]) > mxN) mxN = fabs(yn[i]);
+        }
+        int k = 0;
+        if (rescale)
+          while (mxN > lim * ldexp(D, k) && k < 126) k++;
+        escale += k;
+        for (int i = 0; i < n; i++) {
+          int64_t q = 0;
+          if (k < 40) q = rne_div((int64_t)yn[i], (int64_t)ldexp(D, k));
+          y[i] = (double)(q > 31 ? 31 : (q < -31 ? -31 : q));
+        }
+        t_run = t;
+        ok = or_syndrome_weight(Ho, M, n, c) == 0;
+        if (early_stop && ok) break;
+        continue;
       }
       double mx = 0.0;
       for (int i = 0; i < n; i++) {

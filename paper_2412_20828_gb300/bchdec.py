@@ -89,7 +89,7 @@ class ServeBenchResult(C.Structure):
 class NmsParams(C.Structure):
     _fields_ = [("iters", C.c_int), ("alpha", C.POINTER(C.c_float)), ("n_autos", C.c_int),
                 ("early_stop", C.c_int), ("msg", C.c_int), ("rescale", C.c_int),
-                ("osd_order", C.c_int), ("osd_input", C.c_int)]
+                ("osd_order", C.c_int), ("osd_input", C.c_int), ("qfrac", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -321,11 +321,12 @@ OSD_CHANNEL, OSD_NMS_OUTPUT = 0, 1
 
 
 def params(iters, alpha, n_autos=3, early_stop=True, msg=MSG_FP32, rescale=False, osd_order=2,
-           osd_input=OSD_CHANNEL):
-    """Builds a bch_nms_params; ``alpha`` is a scalar or one factor per iteration."""
+           osd_input=OSD_CHANNEL, qfrac=0):
+    """Builds a bch_nms_params; ``alpha`` is a scalar or one factor per iteration; ``qfrac``
+    fractional bits of the 8-bit form's check-to-variable magnitudes (see the header)."""
     al = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float32), (iters,)))
     p = NmsParams(iters, al.ctypes.data_as(C.POINTER(C.c_float)), n_autos, int(early_stop), msg,
-                  int(rescale), osd_order, int(osd_input))
+                  int(rescale), osd_order, int(osd_input), int(qfrac))
     p._alpha_keepalive = al  # the C struct points into this array
     return p
 

@@ -46,8 +46,8 @@ struct NmsArgs {
   float *ckpt;  // training checkpoints [I+1][F][ld] or null
   unsigned *queue;
   unsigned *check;  // checked builds: the device's check word [4]; else unused
-  int I, early_stop, msg, rescale;
-  float alpha[32];
+  int I, early_stop, msg, rescale, qfrac;
+  float alpha[32];  // alpha_t 2^qfrac
 };
 
 }  // namespace bchlib

@@ -186,6 +186,14 @@ bch_status check_params(const bch_code *code, const bch_nms_params *p) {
   for (int t = 0; t < p->iters; t++)
     if (!std::isfinite(p->alpha[t])) return fail(BCH_EINVAL, "alpha must be finite");
   if (p->osd_input != 0 && p->osd_input != 1) return fail(BCH_EINVAL, "osd_input must be 0 or 1");
+  if (p->qfrac < 0 || p->qfrac > 8) return fail(BCH_EINVAL, "qfrac must be in [0, 8]");
+  if (p->qfrac > 0) {
+    if (p->msg != BCH_MSG_INT8 || p->n_autos < 1)
+      return fail(BCH_EINVAL, "qfrac applies to the enhanced decoder's 8-bit form only");
+    for (int t = 0; t < p->iters; t++)
+      if (!(p->alpha[t] >= 0.0f && p->alpha[t] <= 4.0f))
+        return fail(BCH_EINVAL, "qfrac needs 0 <= alpha_t <= 4 (exact sums)");
+  }
   return BCH_OK;
 }
 
@@ -327,7 +335,9 @@ NmsArgs make_nms_args(const bch_code *code, const bch_nms_params *p, const float
   a.early_stop = p->early_stop ? 1 : 0;
   a.msg = int(p->msg);
   a.rescale = p->rescale ? 1 : 0;
-  for (int t = 0; t < 32; t++) a.alpha[t] = t < p->iters ? p->alpha[t] : 0.0f;
+  a.qfrac = p->qfrac;
+  // with fractional bits the kernels round alpha 2^qfrac min (a power-of-two scale: exact)
+  for (int t = 0; t < 32; t++) a.alpha[t] = t < p->iters ? ldexpf(p->alpha[t], p->qfrac) : 0.0f;
   return a;
 }
 

@@ -157,6 +157,44 @@ __device__ __forceinline__ int8_t to_q(float x) {
   return int8_t(q);
 }
 
+// 8-bit form with qfrac fractional c2v bits: the merged value of a position is the
+// exact numerator N = P 2^qfrac q + sum (an integer below 2^24, so exact in FP32); the
+// stored value is clamp(rne(N / (d 2^k)), +-31), d = P 2^qfrac, after k rescale halvings.
+__device__ __forceinline__ float int8_numerator(int q, int sum, int d) { return float(q * d + sum); }
+// ... and with the rescale on, its input is quantised after the power of two 2^-k0 that
+// keeps max |4x| <= 31 (k0 starts the frame's exponent), so that strong inputs are not
+// clipped at the 8-bit range.
+__device__ __forceinline__ int int8_input_shift(const float *src, int n) {
+  float mx = 0.0f;
+  for (int i = 0; i < n; i++) mx = fmaxf(mx, fabsf(4.0f * src[i]));
+  int k = 0;
+  float lim = 31.0f;
+  while (mx > lim && k < 60) {
+    lim *= 2.0f;
+    k++;
+  }
+  return k;
+}
+// exact integer form (large k only), kept out of line
+static __device__ __noinline__ int int8_quotient_exact(float N, int k, int d) {
+  if (k >= 40) return 0;
+  const long long D = (long long)d << k, n = (long long)N;
+  long long q = n / D, r = n % D;
+  if (r < 0) {
+    r += D;
+    q -= 1;
+  }
+  if (2 * r > D || (2 * r == D && (q & 1))) q += 1;
+  return int(q > 31 ? 31 : (q < -31 ? -31 : q));
+}
+__device__ __forceinline__ int8_t int8_store_quotient(float N, int k, int d) {
+  // A quotient that is not a half-integer lies at least 1 / (2 d 2^k) from one, and the
+  // correctly rounded FP32 quotient errs by at most 2^-20 below 32 (larger ones clamp
+  // to +-31 either way): while d 2^k < 2^19 rounding it gives the exact quotient's rne.
+  if (k < 12 && (d << k) < (1 << 19)) return to_q(__fdiv_rn(N, float(d << k)));
+  return int8_t(int8_quotient_exact(N, k, d));
+}
+
 // Shared-memory carve-up common to the NMS kernels.
 struct GroupDesc {
   int w, rows, off, pad;
@@ -405,6 +443,12 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         t = 0;
         escale = 0;
         const float *src = a.llr + size_t(f) * a.ld;
+        float s4 = 4.0f;  // INT8 input scale: 4 (LSB 1/4), times 2^-k0 (see int8_input_shift)
+        if constexpr (MSG == kINT8)
+          if (a.qfrac && a.rescale) {
+            escale = int8_input_shift(src, n);
+            s4 = ldexpf(4.0f, -escale);
+          }
         for (int i = 0; i < n; i += 4) {
           float4 v;
           if (vec) {
@@ -422,7 +466,7 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
               const float x = vv[h] + 0.0f;  // -0 -> +0: sgn(0) = +1
               if constexpr (MSG == kFP32) y[(i + h) * kShift] = x;
               if constexpr (MSG == kFP16) y[(i + h) * kShift] = to_half_sat(x);
-              if constexpr (MSG == kINT8) y[(i + h) * kShift] = to_q(4.0f * x);
+              if constexpr (MSG == kINT8) y[(i + h) * kShift] = to_q(s4 * x);
               acc[(i + h) * kShift] = A(0);
               if (a.ckpt) a.ckpt[size_t(f) * a.ld + i + h] = x;
             }
@@ -488,7 +532,8 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         if (i < n) {
           float yn;
           if constexpr (MSG == kINT8)
-            yn = float(ld_y(y + (i * kShift))) + __fdiv_rn(float(acc[i * kShift]), fP);
+            yn = a.qfrac ? int8_numerator(ld_y(y + (i * kShift)), acc[i * kShift], a.P << a.qfrac)
+                         : float(ld_y(y + (i * kShift))) + __fdiv_rn(float(acc[i * kShift]), fP);
           else
             yn = __fmaf_rn(ld_y(y + (i * kShift)), fP, acc[i * kShift]);
           cb[i >> 5] |= (__float_as_uint(yn) >> 31) << (i & 31);
@@ -497,23 +542,26 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         }
       }
       // optional power-of-two renormalisation (exact; min-sum is scale invariant):
-      // halve while max |y_new| > lim (FP16: compared on the numerators, exactly)
+      // halve while max |y_new| > lim (FP16 and fractional INT8: compared on the
+      // numerators, exactly)
       float sc = 1.0f;
+      int kr = 0;
       if (a.rescale) {
-        const float lim = (MSG == kINT8) ? 31.0f : 16384.0f * fP;
-        int k = 0;
-        while (mx * sc > lim && k < 126) {
+        const float lim = (MSG == kINT8) ? (a.qfrac ? 31.0f * float(a.P << a.qfrac) : 31.0f) : 16384.0f * fP;
+        while (mx * sc > lim && kr < 126) {
           sc *= 0.5f;
-          k++;
+          kr++;
         }
-        escale += k;
+        escale += kr;
       }
 #pragma unroll
       for (int i = 0; i < NW * 32; i++) {
         if (i < n) {
           const float yn = reinterpret_cast<float *>(acc)[i * kShift] * sc;
           if constexpr (MSG == kINT8)
-            y[i * kShift] = to_q(yn);
+            y[i * kShift] = a.qfrac ? int8_store_quotient(reinterpret_cast<float *>(acc)[i * kShift], kr,
+                                                          a.P << a.qfrac)
+                                    : to_q(yn);
           else
             y[i * kShift] = half_of_quotient(yn, fP);
           acc[i * kShift] = A(0);
@@ -626,6 +674,12 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
         t = 0;
         escale = 0;
         const float *src = a.llr + size_t(f) * a.ld;
+        float s4 = 4.0f;  // as in the one-thread kernel; both halves scan all n inputs
+        if constexpr (MSG == kINT8)
+          if (a.qfrac && a.rescale) {
+            escale = int8_input_shift(src, n);
+            s4 = ldexpf(4.0f, -escale);
+          }
         for (int i = i0; i < i1; i += 4) {
           float4 v;
           if (vec) {
@@ -643,7 +697,7 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
               const float x = vv[q] + 0.0f;  // -0 -> +0: sgn(0) = +1
               if constexpr (MSG == kFP32) y[(i + q) * Fs] = x;
               if constexpr (MSG == kFP16) y[(i + q) * Fs] = to_half_sat(x);
-              if constexpr (MSG == kINT8) y[(i + q) * Fs] = to_q(4.0f * x);
+              if constexpr (MSG == kINT8) y[(i + q) * Fs] = to_q(s4 * x);
               acc[(i + q) * Fs] = A(0);
               if (a.ckpt) a.ckpt[size_t(f) * a.ld + i + q] = x;
             }
@@ -679,7 +733,8 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
         yn = __fmaf_rn(acc[i * Fs], invP, y[i * Fs]);
         y[i * Fs] = yn;
       } else if constexpr (MSG == kINT8) {
-        yn = float(ld_y(y + i * Fs)) + __fdiv_rn(float(acc[i * Fs]), fP);
+        yn = a.qfrac ? int8_numerator(ld_y(y + i * Fs), acc[i * Fs], a.P << a.qfrac)
+                     : float(ld_y(y + i * Fs)) + __fdiv_rn(float(acc[i * Fs]), fP);
         reinterpret_cast<float *>(acc)[i * Fs] = yn;
       } else {
         yn = __fmaf_rn(ld_y(y + i * Fs), fP, acc[i * Fs]);
@@ -707,19 +762,20 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
       }
     } else {
       float sc = 1.0f;
+      int kr = 0;
       if (a.rescale) {
-        const float lim = (MSG == kINT8) ? 31.0f : 16384.0f * fP;
-        int k = 0;
-        while (mx * sc > lim && k < 126) {
+        const float lim = (MSG == kINT8) ? (a.qfrac ? 31.0f * float(a.P << a.qfrac) : 31.0f) : 16384.0f * fP;
+        while (mx * sc > lim && kr < 126) {
           sc *= 0.5f;
-          k++;
+          kr++;
         }
-        escale += k;
+        escale += kr;
       }
       for (int i = i0; i < i1; i++) {
         const float yn = reinterpret_cast<float *>(acc)[i * Fs] * sc;
         if constexpr (MSG == kINT8)
-          y[i * Fs] = to_q(yn);
+          y[i * Fs] = a.qfrac ? int8_store_quotient(reinterpret_cast<float *>(acc)[i * Fs], kr, a.P << a.qfrac)
+                              : to_q(yn);
         else
           y[i * Fs] = half_of_quotient(yn, fP);
         acc[i * Fs] = A(0);

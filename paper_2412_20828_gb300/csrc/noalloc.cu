@@ -6,6 +6,7 @@
 // per-block failure counts, the failed-frame list and its count) lives here in one
 // file-scope __device__ array instead.  Only precompiled kernels are launched (no
 // run-time compilation, so no module is loaded during a call).
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -133,7 +134,8 @@ extern "C" bch_status bch_hybrid_decode_noalloc(const bch_code *code, const bch_
   a.early_stop = p->early_stop ? 1 : 0;
   a.msg = int(p->msg);
   a.rescale = p->rescale ? 1 : 0;
-  for (int t = 0; t < 32; t++) a.alpha[t] = t < p->iters ? p->alpha[t] : 0.0f;
+  a.qfrac = p->qfrac;
+  for (int t = 0; t < 32; t++) a.alpha[t] = t < p->iters ? ldexpf(p->alpha[t], p->qfrac) : 0.0f;
   e = launch_nms(a, st);
   if (e != cudaSuccess) return fail(BCH_ECUDA, std::string("nms kernel: ") + cudaGetErrorString(e));
 

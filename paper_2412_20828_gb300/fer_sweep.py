@@ -20,7 +20,9 @@ import time
 
 import numpy as np
 
-VARIANTS = (("fp32", 0, False), ("fp16", 1, False), ("int8", 2, False), ("int8_rescale", 2, True))
+# (name, message format, power-of-two rescale, fractional c2v bits of the 8-bit form)
+VARIANTS = (("fp32", 0, False, 0), ("fp16", 1, False, 0), ("int8", 2, False, 0), ("int8_rescale", 2, True, 0),
+            ("int8f", 2, False, 8), ("int8f_rescale", 2, True, 8))
 DEFAULT_CODES = ((63, 45), (63, 36))
 DEFAULT_POINTS = tuple(1.0 + 0.5 * i for i in range(11))
 
@@ -80,8 +82,8 @@ def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, 
         its = torch.empty(Fc, dtype=torch.uint8, device="cuda")
         flg = torch.empty(Fc, dtype=torch.uint8, device="cuda")
         ctr = torch.zeros((len(vlist), 2, len(points), 8), dtype=torch.int64, device="cuda")
-        ps = {name: B.params(iters, alpha, n_autos=n_autos, msg=msg, rescale=rs)
-              for name, msg, rs in vlist}
+        ps = {name: B.params(iters, alpha, n_autos=n_autos, msg=msg, rescale=rs, qfrac=qf)
+              for name, msg, rs, qf in vlist}
         ws = B.workspace(code, ps["fp32"], Fc)
         ev = []  # (variant, stage, point, start, end): device time of each decode call
         stream = torch.cuda.current_stream()
@@ -99,7 +101,7 @@ def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, 
                 base = pi * 10**9 + f0
                 B.gen_frames(code, e, e, seed, base, llr[:F], cw[:F])
                 B.draw_automorphisms(n, n_autos, seed + 1, base, aut[:F])
-                for vi, (name, _, _) in enumerate(vlist):
+                for vi, (name, *_) in enumerate(vlist):
                     timed(vi, 0, pi, lambda: B.nms_decode(code, ps[name], llr[:F], aut[:F], hard[:F],
                                                           its[:F], flg[:F], ws=ws))
                     B.count_errors(n, hard[:F], cw[:F], its[:F], flg[:F], ctr[vi, 0, pi])
@@ -113,7 +115,7 @@ def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, 
         for vi, si, pi, a, b in ev:
             dev_s[vi, si, pi] += a.elapsed_time(b) / 1e3
         entry = {"seconds": time.time() - t0, "variants": {}}
-        for vi, (name, _, _) in enumerate(vlist):
+        for vi, (name, *_) in enumerate(vlist):
             v = {}
             for si, stage in enumerate(("nms", "hybrid")):
                 if stage == "hybrid" and not hybrid:
@@ -131,7 +133,7 @@ def run(codes=DEFAULT_CODES, points=DEFAULT_POINTS, frames=1_000_000, iters=12, 
             entry["variants"][name] = v
         for stage in ("nms", "hybrid") if hybrid else ("nms",):
             ref = entry["variants"]["fp32"][stage]["fer"]
-            for name, _, _ in vlist[1:]:
+            for name, *_ in vlist[1:]:
                 v = entry["variants"][name][stage]
                 v["loss_db_vs_fp32"] = fer_loss_db(points, ref, v["fer"], v["frame_errors"])
         res["codes"][f"({n},{k})"] = entry

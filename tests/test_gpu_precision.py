@@ -36,10 +36,10 @@ def torch_cuda():
     return torch
 
 
-def decode(torch, c, llr, autos, iters, msg, rescale, early_stop=True):
+def decode(torch, c, llr, autos, iters, msg, rescale, early_stop=True, qfrac=0):
     F, ld = llr.shape
     p = B.params(iters, ALPHA, n_autos=autos.shape[1], early_stop=early_stop, msg=msg,
-                 rescale=rescale)
+                 rescale=rescale, qfrac=qfrac)
     hard = torch.zeros((F, (c.n + 63) // 64), dtype=torch.int64, device="cuda")
     it = torch.zeros(F, dtype=torch.uint8, device="cuda")
     fl = torch.zeros(F, dtype=torch.uint8, device="cuda")
@@ -64,6 +64,42 @@ def test_int8_bit_exact(torch_cuda, nk, rescale):
     assert np.array_equal(g["hard"], ref["hard"])
     assert np.array_equal(g["flags"] & 1, ref["converged"])
     assert np.array_equal(g["y"].astype(np.float64), ref["y"])
+
+
+@pytest.mark.parametrize("nk", [(63, 36), (63, 45), (127, 64), (127, 99)])
+@pytest.mark.parametrize("rescale", [False, True])
+@pytest.mark.parametrize("kernel", ["jit", "generic"])
+def test_int8_fractional_bit_exact(torch_cuda, nk, rescale, kernel, monkeypatch):
+    """The 8-bit form with 8 fractional c2v bits: integer sums and a merge that rounds
+    the exact quotient, so every output is bit-exact with the oracle's qfrac branch
+    (pinned by hand examples), on the specialised kernels (n = 127: split mapping) and
+    the precompiled one."""
+    if kernel == "generic":
+        monkeypatch.setenv("BCHDEC_NMS_KERNEL", "generic")
+    n, k = nk
+    c = B.Code(n, k)
+    F = 800
+    cw, llr = frames(n, k, F, 3.0, 1900 + n + k, ld=(n + 3) & ~3)
+    autos = O.draw_autos(n, 3, 41, 0, F)
+    g = decode(torch_cuda, c, llr, autos, 12, B.MSG_INT8, rescale, qfrac=8)
+    ref = O.nms_enhanced_q(c.dense(), llr, autos, 12, ALPHA, 2, rescale=rescale, threads=None,
+                           qfrac=8)
+    assert np.array_equal(g["iters"], ref["iters"])
+    assert np.array_equal(g["hard"], ref["hard"])
+    assert np.array_equal(g["flags"] & 1, ref["converged"])
+    assert np.array_equal(g["y"].astype(np.float64), ref["y"])
+
+
+def test_fractional_bits_rejected_outside_the_8_bit_form(torch_cuda):
+    c = B.Code(63, 45)
+    for kw in (dict(msg=B.MSG_FP32, qfrac=8), dict(msg=B.MSG_INT8, qfrac=9),
+               dict(msg=B.MSG_INT8, qfrac=8, n_autos=0)):
+        p = B.params(4, ALPHA, **{"n_autos": 3, **kw})
+        with pytest.raises(B.BchError) as e:
+            B.nms_decode(
+                c, p, to_dev(np.zeros((4, 64), np.float32)), autos_dev(np.zeros((4, 3), np.uint16)),
+                torch_cuda.zeros((4, 1), dtype=torch_cuda.int64, device="cuda"))
+        assert e.value.status == B.EINVAL
 
 
 @pytest.mark.parametrize("nk,ebn0", [((63, 45), 2.5), ((127, 64), 3.5), ((127, 99), 3.5)])

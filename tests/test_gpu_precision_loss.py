@@ -10,8 +10,9 @@ reference is the FP64 curve where that curve is resolved (>= 50 errors at both e
 the interpolation); at the high-SNR points the oracle sample holds too few errors, and
 the reference there is the GPU's FP32 curve, which takes the FP64 decisions frame by
 frame: on the oracle's sample the two differ by no more than the frames whose decoding
-met a sign-ambiguous value.  FP16 must stay within 0.1 dB wherever the loss is
-resolved; the 8-bit forms' losses are reported."""
+met a sign-ambiguous value.  FP16 and the 8-bit form with 8 fractional check-to-variable
+bits and the power-of-two rescale (int8f_rescale) must stay within 0.1 dB wherever the
+loss is resolved; the other 8-bit forms' losses are reported."""
 import math
 
 import numpy as np
@@ -61,7 +62,7 @@ def test_reduced_precision_loss_against_fp64(nk):
         sd = math.sqrt(max(p * (1 - p), 1.0 / ORACLE_FRAMES) / ORACLE_FRAMES)
         assert abs(g32["fer"][pi] - p) <= 4 * sd + 1e-6, (POINTS[pi], g32["fer"][pi], p)
     table = {}
-    for name in ("fp16", "int8", "int8_rescale"):
+    for name in ("fp16", "int8", "int8_rescale", "int8f", "int8f_rescale"):
         s = var[name]["nms"]
         losses = []
         for pi, e in enumerate(POINTS):
@@ -81,3 +82,6 @@ def test_reduced_precision_loss_against_fp64(nk):
     for name, losses in table.items():
         print(f"  {name}: {losses}")
     assert all(x is None or x[0] <= 0.1 for x in table["fp16"])
+    # the 8-bit form with fractional c2v bits and the power-of-two rescale (input and
+    # merges) stays within 0.1 dB as well
+    assert all(x is None or x[0] <= 0.1 for x in table["int8f_rescale"])
