@@ -17,7 +17,7 @@
 using namespace bchlib;
 
 namespace bchlib {
-cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err);
+cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err, int qfrac = 0);
 bool jit_compile_check(const bch_code *c, int msg, std::string *log);
 bool jit_serve_compile_check(const bch_code *const *codes, int n_codes, std::string *log);
 int jit_block_size(int n);
@@ -709,7 +709,7 @@ static cudaError_t launch_nms_code(const bch_code *code, const NmsArgs &a, cudaS
   // cached on disk); auto falls back to the precompiled kernel if it does not compile
   if (a.P > 0 && mode != 1) {
     std::string err;
-    cudaKernel_t k = jit_kernel(code, a.msg, &err);
+    cudaKernel_t k = jit_kernel(code, a.msg, &err, a.qfrac);
     if (k) return launch_jit(k, code, a, st);
     if (why) *why = err;
     if (mode == 2) return cudaErrorNotSupported;

@@ -503,7 +503,7 @@ std::string jit_serve_blocks_source(const bch_code *const *codes, int n_codes) {
   return o.str();
 }
 
-std::string jit_source(const bch_code *c, int msg) {
+static std::string jit_body_source(const bch_code *c, int msg) {
   if (jit_split(c->alg.n)) return jit_split_source(c, msg);
   const int n = c->alg.n;
   const int tpb = jit_block_size(n);
@@ -614,7 +614,7 @@ static void write_file_atomic(const std::string &path, const std::vector<char> &
 
 // Returns the specialised kernel for (code, msg), compiling it on first use (or
 // loading it from the on-disk cache); on failure returns nullptr and sets *err.
-cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err);
+cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err, int qfrac);
 
 // The tuning knobs that shape the generated source (read from the environment).
 static std::string jit_knob_signature(int n) {
@@ -626,8 +626,14 @@ static std::string jit_knob_signature(int n) {
   return buf;
 }
 
-cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
-  const std::string key = std::to_string(msg) + ":" + jit_knob_signature(c->alg.n);
+// The batch kernel's source for code c, format msg and qfrac fractional c2v bits (a
+// compile-time constant, so the other forms carry none of its branches).
+std::string jit_source(const bch_code *c, int msg, int qfrac) {
+  return "#define BCH_JIT_QFRAC " + std::to_string(qfrac) + "\n" + jit_body_source(c, msg);
+}
+
+cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err, int qfrac) {
+  const std::string key = std::to_string(msg) + "/" + std::to_string(qfrac) + ":" + jit_knob_signature(c->alg.n);
   {
     std::lock_guard<std::mutex> lk(c->jit_mu);
     for (const auto &m : c->jit_memo)
@@ -637,7 +643,7 @@ cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err) {
       }
   }
   std::string why;
-  cudaKernel_t k = jit_kernel_from_source(c, msg, &why);
+  cudaKernel_t k = jit_kernel_from_source(c, msg, &why, qfrac);
   {
     std::lock_guard<std::mutex> lk(c->jit_mu);
     c->jit_memo.push_back({key, static_cast<void *>(k), why});
@@ -724,8 +730,8 @@ static cudaKernel_t compile_source(const std::string &src_in, const char *entry,
   return cp->kernel;
 }
 
-cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err) {
-  return compile_source(jit_source(c, msg), "bch_nms_jit", err);
+cudaKernel_t jit_kernel_from_source(const bch_code *c, int msg, std::string *err, int qfrac) {
+  return compile_source(jit_source(c, msg, qfrac), "bch_nms_jit", err);
 }
 
 cudaKernel_t jit_serve_kernel(const bch_code *const *codes, int n_codes, std::string *err) {
@@ -741,7 +747,7 @@ cudaKernel_t jit_serve_blocks_kernel(const bch_code *const *codes, int n_codes, 
 static bool compile_check_source(const std::string &src, const char *entry, std::string *log);
 
 bool jit_compile_check(const bch_code *c, int msg, std::string *log) {
-  return compile_check_source(jit_source(c, msg), "bch_nms_jit", log);
+  return compile_check_source(jit_source(c, msg, 0), "bch_nms_jit", log);
 }
 
 bool jit_serve_compile_check(const bch_code *const *codes, int n_codes, std::string *log) {

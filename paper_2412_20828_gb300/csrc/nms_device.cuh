@@ -160,6 +160,13 @@ __device__ __forceinline__ int8_t to_q(float x) {
 // 8-bit form with qfrac fractional c2v bits: the merged value of a position is the
 // exact numerator N = P 2^qfrac q + sum (an integer below 2^24, so exact in FP32); the
 // stored value is clamp(rne(N / (d 2^k)), +-31), d = P 2^qfrac, after k rescale halvings.
+// The fractional bits in force: a compile-time constant in kernels compiled for one
+// value (the run-time specialised ones define BCH_JIT_QFRAC), else the argument.
+#ifdef BCH_JIT_QFRAC
+#define BCH_QFRAC(a) (BCH_JIT_QFRAC)
+#else
+#define BCH_QFRAC(a) ((a).qfrac)
+#endif
 __device__ __forceinline__ float int8_numerator(int q, int sum, int d) { return float(q * d + sum); }
 // ... and with the rescale on, its input is quantised after the power of two 2^-k0 that
 // keeps max |4x| <= 31 (k0 starts the frame's exponent), so that strong inputs are not
@@ -445,7 +452,7 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         const float *src = a.llr + size_t(f) * a.ld;
         float s4 = 4.0f;  // INT8 input scale: 4 (LSB 1/4), times 2^-k0 (see int8_input_shift)
         if constexpr (MSG == kINT8)
-          if (a.qfrac && a.rescale) {
+          if (BCH_QFRAC(a) && a.rescale) {
             escale = int8_input_shift(src, n);
             s4 = ldexpf(4.0f, -escale);
           }
@@ -532,7 +539,7 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         if (i < n) {
           float yn;
           if constexpr (MSG == kINT8)
-            yn = a.qfrac ? int8_numerator(ld_y(y + (i * kShift)), acc[i * kShift], a.P << a.qfrac)
+            yn = BCH_QFRAC(a) ? int8_numerator(ld_y(y + (i * kShift)), acc[i * kShift], a.P << BCH_QFRAC(a))
                          : float(ld_y(y + (i * kShift))) + __fdiv_rn(float(acc[i * kShift]), fP);
           else
             yn = __fmaf_rn(ld_y(y + (i * kShift)), fP, acc[i * kShift]);
@@ -547,7 +554,7 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
       float sc = 1.0f;
       int kr = 0;
       if (a.rescale) {
-        const float lim = (MSG == kINT8) ? (a.qfrac ? 31.0f * float(a.P << a.qfrac) : 31.0f) : 16384.0f * fP;
+        const float lim = (MSG == kINT8) ? (BCH_QFRAC(a) ? 31.0f * float(a.P << BCH_QFRAC(a)) : 31.0f) : 16384.0f * fP;
         while (mx * sc > lim && kr < 126) {
           sc *= 0.5f;
           kr++;
@@ -559,8 +566,8 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
         if (i < n) {
           const float yn = reinterpret_cast<float *>(acc)[i * kShift] * sc;
           if constexpr (MSG == kINT8)
-            y[i * kShift] = a.qfrac ? int8_store_quotient(reinterpret_cast<float *>(acc)[i * kShift], kr,
-                                                          a.P << a.qfrac)
+            y[i * kShift] = BCH_QFRAC(a) ? int8_store_quotient(reinterpret_cast<float *>(acc)[i * kShift], kr,
+                                                          a.P << BCH_QFRAC(a))
                                     : to_q(yn);
           else
             y[i * kShift] = half_of_quotient(yn, fP);
@@ -676,7 +683,7 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
         const float *src = a.llr + size_t(f) * a.ld;
         float s4 = 4.0f;  // as in the one-thread kernel; both halves scan all n inputs
         if constexpr (MSG == kINT8)
-          if (a.qfrac && a.rescale) {
+          if (BCH_QFRAC(a) && a.rescale) {
             escale = int8_input_shift(src, n);
             s4 = ldexpf(4.0f, -escale);
           }
@@ -733,7 +740,7 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
         yn = __fmaf_rn(acc[i * Fs], invP, y[i * Fs]);
         y[i * Fs] = yn;
       } else if constexpr (MSG == kINT8) {
-        yn = a.qfrac ? int8_numerator(ld_y(y + i * Fs), acc[i * Fs], a.P << a.qfrac)
+        yn = BCH_QFRAC(a) ? int8_numerator(ld_y(y + i * Fs), acc[i * Fs], a.P << BCH_QFRAC(a))
                      : float(ld_y(y + i * Fs)) + __fdiv_rn(float(acc[i * Fs]), fP);
         reinterpret_cast<float *>(acc)[i * Fs] = yn;
       } else {
@@ -764,7 +771,7 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
       float sc = 1.0f;
       int kr = 0;
       if (a.rescale) {
-        const float lim = (MSG == kINT8) ? (a.qfrac ? 31.0f * float(a.P << a.qfrac) : 31.0f) : 16384.0f * fP;
+        const float lim = (MSG == kINT8) ? (BCH_QFRAC(a) ? 31.0f * float(a.P << BCH_QFRAC(a)) : 31.0f) : 16384.0f * fP;
         while (mx * sc > lim && kr < 126) {
           sc *= 0.5f;
           kr++;
@@ -774,7 +781,7 @@ __device__ __forceinline__ void nms_split_persistent(const NmsArgs &a, unsigned 
       for (int i = i0; i < i1; i++) {
         const float yn = reinterpret_cast<float *>(acc)[i * Fs] * sc;
         if constexpr (MSG == kINT8)
-          y[i * Fs] = a.qfrac ? int8_store_quotient(reinterpret_cast<float *>(acc)[i * Fs], kr, a.P << a.qfrac)
+          y[i * Fs] = BCH_QFRAC(a) ? int8_store_quotient(reinterpret_cast<float *>(acc)[i * Fs], kr, a.P << BCH_QFRAC(a))
                               : to_q(yn);
         else
           y[i * Fs] = half_of_quotient(yn, fP);
