@@ -139,15 +139,27 @@ __device__ __forceinline__ int rne_product(float alpha, int m) {
   return int(r);
 }
 // FP16: the binary16 value nearest to alpha m (ties to even, saturating at +-65504),
-// returned as a float.
+// returned as a float.  The product is first rounded to odd in FP32 -- an inexact hi
+// (lo != 0) is replaced by its FP32 neighbour toward zero with the last bit set -- and
+// that value is rounded to nearest binary16 once.  FP32 keeps at least 13 bits beyond
+// binary16's 11 (more in binary16's subnormal range), and a double rounding whose first
+// step rounds to odd with at least two extra bits gives the single rounding of the
+// exact product (Boldo and Melquiond, "Emulation of FMA and correctly rounded sums:
+// proved algorithms using rounding to odd", IEEE Trans. Computers 57(4), 2008).  Values
+// at or past 65504 saturate.  One conversion instead of three keeps the per-row code of
+// the row-specialised kernels short.
 __device__ __forceinline__ float half_product(float alpha, float m) {
   const float hi = alpha * m, lo = __fmaf_rn(alpha, m, -hi);
-  if (fabsf(hi) >= 65504.0f) return copysignf(65504.0f, hi);
-  const __half dn = __float2half_rd(hi), up = __float2half_ru(hi);
-  const float fdn = __half2float(dn), fup = __half2float(up);
-  float r = __half2float(__float2half_rn(hi));
-  if (fdn != fup && hi == 0.5f * (fdn + fup)) r = lo > 0.0f ? fup : (lo < 0.0f ? fdn : r);
-  return r;
+  uint32_t b = __float_as_uint(hi);
+  if (lo != 0.0f) {
+    // hi is on the far side of the exact product iff lo has the opposite sign (RN keeps
+    // the sign of the product, so hi is not a zero here unless the product underflows,
+    // and then lo has the same sign)
+    if ((__float_as_uint(lo) ^ b) & kSign) b -= 1u;
+    b |= 1u;
+  }
+  const float ro = fminf(fmaxf(__uint_as_float(b), -65504.0f), 65504.0f);
+  return __half2float(__float2half_rn(ro));
 }
 
 // INT8 store: rne, saturating at +-31 (LSB = 1/4 of an LLR unit).
