@@ -125,36 +125,36 @@ __device__ __forceinline__ __half half_of_quotient(float num, float P) {
 // Check-to-variable magnitudes of the reduced formats, rounded once from the exact
 // product alpha * m without FP64 arithmetic (which runs at a small fraction of the FP32
 // rate): hi = fl(alpha m) and lo = fma(alpha, m, -hi) = alpha m - hi exactly (the
-// error-free product).  hi lies on the same side of every rounding point as the exact
-// product (RN is monotone and those points are FP32 values), so rounding hi is right
-// unless hi landed exactly on a rounding point; then lo says which side the exact
-// product is on.
-// INT8: rne(alpha m) for an integer m, as an int.
+// error-free product).  The product rounded to odd in FP32 -- an inexact hi (lo != 0)
+// replaced by its FP32 neighbour toward zero with the last bit set; hi is on the far
+// side of the exact product iff lo has the opposite sign -- rounded once more to the
+// target format equals the exact product rounded to that format, as long as FP32 keeps
+// at least two bits beyond the target's precision (Boldo and Melquiond, "Emulation of
+// FMA and correctly rounded sums: proved algorithms using rounding to odd", IEEE
+// Trans. Computers 57(4), 2008).  One conversion does the final rounding.
+// INT8: rne(alpha m) for an integer m, as an int; exact while |alpha m| < 2^22 (two
+// bits below the integer point; the 8-bit forms' products stay below 2^15).
 __device__ __forceinline__ int rne_product(float alpha, int m) {
   const float b = float(m);
   const float hi = alpha * b, lo = __fmaf_rn(alpha, b, -hi);
-  const float fl = floorf(hi);
-  float r = rintf(hi);
-  if (hi - fl == 0.5f) r = lo > 0.0f ? fl + 1.0f : (lo < 0.0f ? fl : r);
-  return int(r);
+  uint32_t u = __float_as_uint(hi);
+  if (lo != 0.0f) {
+    if ((__float_as_uint(lo) ^ u) & kSign) u -= 1u;
+    u |= 1u;
+  }
+  return __float2int_rn(__uint_as_float(u));
 }
 // FP16: the binary16 value nearest to alpha m (ties to even, saturating at +-65504),
-// returned as a float.  The product is first rounded to odd in FP32 -- an inexact hi
-// (lo != 0) is replaced by its FP32 neighbour toward zero with the last bit set -- and
-// that value is rounded to nearest binary16 once.  FP32 keeps at least 13 bits beyond
-// binary16's 11 (more in binary16's subnormal range), and a double rounding whose first
-// step rounds to odd with at least two extra bits gives the single rounding of the
-// exact product (Boldo and Melquiond, "Emulation of FMA and correctly rounded sums:
-// proved algorithms using rounding to odd", IEEE Trans. Computers 57(4), 2008).  Values
-// at or past 65504 saturate.  One conversion instead of three keeps the per-row code of
-// the row-specialised kernels short.
+// returned as a float; FP32 keeps at least 13 bits beyond binary16's 11 (more in
+// binary16's subnormal range).  One conversion instead of three keeps the per-row code
+// of the row-specialised kernels short.
 __device__ __forceinline__ float half_product(float alpha, float m) {
   const float hi = alpha * m, lo = __fmaf_rn(alpha, m, -hi);
   uint32_t b = __float_as_uint(hi);
   if (lo != 0.0f) {
-    // hi is on the far side of the exact product iff lo has the opposite sign (RN keeps
-    // the sign of the product, so hi is not a zero here unless the product underflows,
-    // and then lo has the same sign)
+    // hi is on the far side of the exact product iff lo has the opposite sign; hi is
+    // not zero here (a product that rounds to zero leaves lo = 0 too: the FMA rounds
+    // the same product)
     if ((__float_as_uint(lo) ^ b) & kSign) b -= 1u;
     b |= 1u;
   }
