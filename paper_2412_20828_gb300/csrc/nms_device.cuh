@@ -103,23 +103,23 @@ __device__ __forceinline__ __half to_half_sat(float x) {
   return half_pz(__float2half_rn(x));
 }
 // FP16 merge: the binary16 value nearest to num / P (num = P y + sum of c2v), ties
-// to even, saturating at +-65504, with num exact.  The FP32 quotient q = fl(num / P)
-// lies on the same side of every binary16 rounding point as the exact quotient (RN is
-// monotone and those points are FP32 values), so rounding q gives the right result
-// unless q landed exactly on a midpoint the exact quotient is not on; then the sign
-// of num - mid P (an exact product, one rounding that keeps the sign) picks the side.
+// to even, saturating at +-65504, with num exact.  The correctly rounded FP32 quotient
+// q leaves an exactly representable remainder r = num - q P (one FMA), whose sign says
+// on which side of q the exact quotient lies; q rounded to odd on that information and
+// then rounded once to binary16 is the exact quotient's binary16 rounding (the
+// round-to-odd rule of the check-to-variable roundings below: FP32 keeps at least 13
+// bits beyond binary16's 11).  One conversion.
 __device__ __forceinline__ __half half_of_quotient(float num, float P) {
   const float q = __fdiv_rn(num, P);
-  if (fabsf(q) >= 65504.0f) return __float2half_rn(copysignf(65504.0f, q));
-  const __half lo = __float2half_rd(q), hi = __float2half_ru(q);
-  const float mid = 0.5f * (__half2float(lo) + __half2float(hi));
-  __half h = __float2half_rn(q);
-  if (q == mid && __half2float(lo) != __half2float(hi)) {
-    const float d = __fmaf_rn(-mid, P, num);
-    if (d > 0.0f) h = hi;
-    if (d < 0.0f) h = lo;
+  const float r = __fmaf_rn(-q, P, num);
+  uint32_t b = __float_as_uint(q);
+  if (r != 0.0f) {
+    // the exact quotient q + r / P is nearer zero than q iff r and q differ in sign
+    if ((__float_as_uint(r) ^ b) & kSign) b -= 1u;
+    b |= 1u;
   }
-  return half_pz(h);
+  const float ro = fminf(fmaxf(__uint_as_float(b), -65504.0f), 65504.0f);
+  return half_pz(__float2half_rn(ro));
 }
 
 // Check-to-variable magnitudes of the reduced formats, rounded once from the exact

@@ -1,6 +1,8 @@
-// Test driver: out[i] = half_product(alpha[i], m[i]) from the decoder's device header
-// (the FP16 form's check-to-variable rounding), for tests/test_gpu_half_product.py.
-// Input file: int32 N, float32 alpha[N], float32 m[N]; output file: float32 out[N].
+// Test driver for tests/test_gpu_half_product.py: the FP16 form's roundings from the
+// decoder's device header.  Mode "product": out[i] = half_product(a[i], b[i]) (the
+// check-to-variable rounding of alpha m); mode "quotient": out[i] =
+// half_of_quotient(a[i], b[i]) (the merge's rounding of num / P).
+// Input file: int32 N, float32 a[N], float32 b[N]; output file: float32 out[N].
 #include <cstdio>
 #include <vector>
 
@@ -8,13 +10,15 @@
 
 #include "nms_device.cuh"
 
-__global__ void half_product_kernel(const float *alpha, const float *m, float *out, int N) {
+__global__ void half_round_kernel(const float *a, const float *b, float *out, int N, int quotient) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) out[i] = bchlib::half_product(alpha[i], m[i]);
+  if (i < N)
+    out[i] = quotient ? __half2float(bchlib::half_of_quotient(a[i], b[i])) : bchlib::half_product(a[i], b[i]);
 }
 
 int main(int argc, char **argv) {
-  if (argc != 3) return 2;
+  if (argc != 4) return 2;
+  const int quotient = argv[3][0] == 'q' ? 1 : 0;
   FILE *fi = std::fopen(argv[1], "rb");
   if (!fi) return 2;
   int N = 0;
@@ -28,7 +32,7 @@ int main(int argc, char **argv) {
     return 3;
   cudaMemcpy(da, a.data(), 4 * size_t(N), cudaMemcpyHostToDevice);
   cudaMemcpy(dm, m.data(), 4 * size_t(N), cudaMemcpyHostToDevice);
-  half_product_kernel<<<(N + 255) / 256, 256>>>(da, dm, dout, N);
+  half_round_kernel<<<(N + 255) / 256, 256>>>(da, dm, dout, N, quotient);
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return 4;
   cudaMemcpy(o.data(), dout, 4 * size_t(N), cudaMemcpyDeviceToHost);
