@@ -101,6 +101,7 @@ const char *row_macros(int msg) {
 #define BCH_RM(SG) const int c1_ = rne_product(alpha, m1_); const int c2_ = rne_product(alpha, m2_); \
   const bool neg_ = (SG); const int v1_ = neg_ ? -c1_ : c1_; const int dv_ = (neg_ ? -c2_ : c2_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
+#define BCH_R2I(u) BCH_SV(u) = v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) BCH_R2(u)
 #define BCH_RE }
 #define BCH_FIN(u) ((z[u] < 0) ? -BCH_SV(u) : BCH_SV(u))
@@ -121,6 +122,7 @@ const char *row_macros(int msg) {
   const float v1_ = flip_sign(half_product(alpha, m1_), sg_); \
   const float dv_ = flip_sign(half_product(alpha, m2_), sg_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
+#define BCH_R2I(u) BCH_SV(u) = v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) { const float p_ = (fabsf(z[u]) - m1_) * 0x1p100f; \
   BCH_SV(u) = __fmaf_rn(dv_, __saturatef(__fmaf_rn(-p_, 0x1p100f, 1.0f)), BCH_SV(u) + v1_); }
 #define BCH_RE }
@@ -140,6 +142,7 @@ const char *row_macros(int msg) {
 #define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
   const float v1_ = flip_sign(alpha * m1_, sg_); const float dv_ = flip_sign(alpha * m2_, sg_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
+#define BCH_R2I(u) BCH_SV(u) = v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) { const float p_ = (fabsf(z[u]) - m1_) * 0x1p100f; \
   BCH_SV(u) = __fmaf_rn(dv_, __saturatef(__fmaf_rn(-p_, 0x1p100f, 1.0f)), BCH_SV(u) + v1_); }
 #define BCH_RE }
@@ -267,6 +270,10 @@ static void emit_prologue(std::ostringstream &o, int msg, bool serving) {
 // multiply -- the same positions.  Measured on the config-2 mix: FP32 0.540 of the
 // peak against 0.515 (FP16 +5%, INT8 +1.5%); BCHDEC_JIT_INCR=0 restores the direct form.
 bool jit_incr() { return env_int("BCHDEC_JIT_INCR", 0, 1, 1) == 1; }
+// The first row of a column assigns its row sum instead of adding to zero (the same
+// value but for the sign of a zero, which the accumulator, +0 at each iteration, cannot
+// see); BCHDEC_JIT_FIRST_ASSIGN=0 adds as the rows after it do (a tuning knob).
+bool jit_first_assign() { return env_int("BCHDEC_JIT_FIRST_ASSIGN", 0, 1, 1) == 1; }
 
 // The four running offsets o0_..o3_ of variables u0..u0 + 3 and their common step st4_
 // (stride: a C expression; u0 u 2^-j is formed by doubling and adding at emission).
@@ -335,6 +342,7 @@ static void emit_copy_body(std::ostringstream &o, const bch_code *c, int msg, in
   // overlapping the shared-memory row sums of many rows (n = 127: 0.55 KB of spills
   // instead of 2.5 KB, but measured 4% slower, so off by default)
   const bool fence = env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, 0) == 1;
+  std::vector<char> touched(n, 0);
   for (const Row &row : c->rows) {
     std::vector<int> cols;
     for (int u = 0; u < n; u++)
@@ -373,7 +381,14 @@ static void emit_copy_body(std::ostringstream &o, const bch_code *c, int msg, in
       fma_acc += fma_pct;
       const bool f = fma_acc >= 100;
       if (f) fma_acc -= 100;
-      o << (f ? " BCH_R2F(" : " BCH_R2(") << cols[q] << ")";
+      // the first row of a column assigns its row sum: 0 + v1 = v1 but for the sign of a
+      // zero, which no later addition to the accumulator (+0 at each iteration) can see
+      if (!touched[cols[q]] && jit_first_assign()) {
+        touched[cols[q]] = 1;
+        o << " BCH_R2I(" << cols[q] << ")";
+      } else {
+        o << (f ? " BCH_R2F(" : " BCH_R2(") << cols[q] << ")";
+      }
     }
     o << " BCH_RE" << (fence ? " asm volatile(\"\" ::: \"memory\");" : "") << "\n";
   }
@@ -481,12 +496,16 @@ static void emit_split_half(std::ostringstream &o, const bch_code *c, int msg, i
       o << " BCH_PS(" << buf << ", " << (r - ch * R) << ", " << par[r] << ") BCH_RE\n";
     }
   };
+  std::vector<char> touched(nh, 0);  // first row of a column assigns (see emit_copy_body)
   auto pass2 = [&](int ch) {
     const char *buf = (ch & 1) ? "pb" : "pa";
     for (int r = ch * R; r < std::min(M, ch * R + R); r++) {
       if (cols[r].empty()) continue;  // no edge of this half: nothing to add
       o << "  BCH_R0 BCH_Q(" << buf << ", " << (r - ch * R) << ") BCH_RM(sgp_)";
-      for (int u : cols[r]) o << " BCH_R2(" << u << ")";
+      for (int u : cols[r]) {
+        o << (touched[u] || !jit_first_assign() ? " BCH_R2(" : " BCH_R2I(") << u << ")";
+        touched[u] = 1;
+      }
       o << " BCH_RE\n";
     }
   };
@@ -692,7 +711,7 @@ static std::string jit_knob_signature(int n) {
   std::snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d", jit_block_size(n), jit_min_blocks(n),
                 int(jit_pairs()) + 2 * jit_chains(),
                 jit_fma_percent(), env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, 0), jit_scratch_words(n),
-                int(jit_split(n)) + 2 * int(jit_incr()));
+                int(jit_split(n)) + 2 * int(jit_incr()) + 4 * int(jit_first_assign()));
   return buf;
 }
 
