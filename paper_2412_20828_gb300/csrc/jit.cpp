@@ -274,6 +274,19 @@ bool jit_incr() { return env_int("BCHDEC_JIT_INCR", 0, 1, 1) == 1; }
 // value but for the sign of a zero, which the accumulator, +0 at each iteration, cannot
 // see); BCHDEC_JIT_FIRST_ASSIGN=0 adds as the rows after it do (a tuning knob).
 bool jit_first_assign() { return env_int("BCHDEC_JIT_FIRST_ASSIGN", 0, 1, 1) == 1; }
+// The lockstep kernel synchronises its block once per iteration; a block barrier before
+// each automorphism copy as well (BCHDEC_JIT_COPY_BARRIER=1, a knob) measured 0.5%
+// slower on the config-2 mix: a copy touches only its thread's columns.
+bool jit_copy_barrier() { return env_int("BCHDEC_JIT_COPY_BARRIER", 0, 1, 0) == 1; }
+// The statement that builds the sign words ng[] of count variables z[0..count): bit
+// u & 31 of word u >> 5 is the sign of z_u.
+static std::string sign_word_loop(int count, int msg, const char *indent) {
+  const std::string bits = msg == 2 ? "uint32_t(z[u])" : "__float_as_uint(z[u])";
+  std::ostringstream o;
+  o << "#pragma unroll\n" << indent << "for (int u = 0; u < " << count << "; u++) ng[u >> 5] |= (" << bits
+    << " >> 31) << (u & 31);\n";
+  return o.str();
+}
 
 // The four running offsets o0_..o3_ of variables u0..u0 + 3 and their common step st4_
 // (stride: a C expression; u0 u 2^-j is formed by doubling and adding at emission).
@@ -333,8 +346,7 @@ static void emit_copy_body(std::ostringstream &o, const bch_code *c, int msg, in
       << "; u++) S[u] = 0;\n";
   // sign mask of the permuted word: bit u = [z_u < 0]
   o << "    uint32_t ng[" << nw << "];\n#pragma unroll\n    for (int w = 0; w < " << nw << "; w++) ng[w] = 0u;\n"
-    << "#pragma unroll\n    for (int u = 0; u < " << n << "; u++) ng[u >> 5] |= "
-    << (msg == 2 ? "(uint32_t(z[u]) >> 31)" : "(__float_as_uint(z[u]) >> 31)") << " << (u & 31);\n";
+    << sign_word_loop(n, msg, "    ");
   // rows, grouped by weight like the device image
   const int fma_pct = jit_fma_percent();
   int fma_acc = 0;
@@ -458,8 +470,7 @@ static void emit_split_half(std::ostringstream &o, const bch_code *c, int msg, i
     << "  StoreT<" << msg << ">::A S[" << nh << "];\n#pragma unroll\n  for (int u = 0; u < " << nh
     << "; u++) S[u] = 0;\n"
     << "  uint32_t ng[" << nwh << "];\n#pragma unroll\n  for (int w = 0; w < " << nwh << "; w++) ng[w] = 0u;\n"
-    << "#pragma unroll\n  for (int u = 0; u < " << nh << "; u++) ng[u >> 5] |= "
-    << (msg == 2 ? "(uint32_t(z[u]) >> 31)" : "(__float_as_uint(z[u]) >> 31)") << " << (u & 31);\n";
+    << sign_word_loop(nh, msg, "  ");
   // the half's columns (local indices) and its sign-parity expression, per row
   const int M = int(c->rows.size());
   std::vector<std::vector<int>> cols(M);
@@ -711,14 +722,17 @@ static std::string jit_knob_signature(int n) {
   std::snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d", jit_block_size(n), jit_min_blocks(n),
                 int(jit_pairs()) + 2 * jit_chains(),
                 jit_fma_percent(), env_int("BCHDEC_JIT_ROW_FENCE", 0, 1, 0), jit_scratch_words(n),
-                int(jit_split(n)) + 2 * int(jit_incr()) + 4 * int(jit_first_assign()));
+                int(jit_split(n)) + 2 * int(jit_incr()) + 4 * int(jit_first_assign()) +
+                    8 * int(jit_copy_barrier()));
   return buf;
 }
 
 // The batch kernel's source for code c, format msg and qfrac fractional c2v bits (a
 // compile-time constant, so the other forms carry none of its branches).
 std::string jit_source(const bch_code *c, int msg, int qfrac) {
-  return "#define BCH_JIT_QFRAC " + std::to_string(qfrac) + "\n" + jit_body_source(c, msg);
+  return "#define BCH_JIT_QFRAC " + std::to_string(qfrac) + "\n" +
+         (jit_copy_barrier() ? std::string() : std::string("#define BCH_JIT_NO_COPY_BARRIER 1\n")) +
+         jit_body_source(c, msg);
 }
 
 cudaKernel_t jit_kernel(const bch_code *c, int msg, std::string *err, int qfrac) {

@@ -422,10 +422,11 @@ __device__ __forceinline__ int pull_frame(unsigned *queue, bool need, int F) {
 // kernels; `copy` processes one automorphism of one frame (check pass + accumulate).
 // Per-thread shared columns (stride = block size): ctx[P], acc[n], y[n], then
 // Copy::kScratch words of scratch for the functor.  TPBC: compile-time block size (0 =
-// blockDim.x).  LOCKSTEP: the block's warps start every automorphism together (a
-// barrier per copy) and lanes without a frame run it on their stale column, so all
-// warps of the block stream through the same code -- for long straight-line copy code
-// this keeps the instruction cache warm.
+// blockDim.x).  LOCKSTEP: the block's warps start every iteration together (a barrier
+// per iteration, and one per automorphism copy unless the run-time specialised kernel
+// defines BCH_JIT_NO_COPY_BARRIER) and lanes without a frame run the copies on their
+// stale columns, so all warps of the block stream through the same code -- for long
+// straight-line copy code this keeps the instruction cache warm.
 template <int MSG, int NW, bool LOCKSTEP, int TPBC, class Copy>
 __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *smem, const Copy &copy) {
   using Y = typename StoreT<MSG>::Y;
@@ -510,7 +511,9 @@ __device__ __forceinline__ void nms_persistent(const NmsArgs &a, unsigned char *
 
     const float alpha = tb.alpha[f >= 0 ? t : 0];
     for (int p = 0; p < a.P; p++) {
+#ifndef BCH_JIT_NO_COPY_BARRIER
       if constexpr (LOCKSTEP) __syncthreads();
+#endif
       const uint32_t cx = f >= 0 ? ctx[p * kShift] : 0u;
       copy(tb, n_groups, uint32_t(n), m, y, acc, scratch, cx & 0xffu, cx >> 8, uint32_t(kShift), alpha);
     }
