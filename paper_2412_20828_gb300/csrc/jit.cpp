@@ -82,7 +82,7 @@ NvrtcApi &nvrtc() {
 // product of the whole row: the rows accumulate T[u] = sum_j sg_j alpha m_j(u) and the
 // factor sgn(z_u) is applied once per variable at the end.  sg_j is the parity of the
 // row's negative entries, taken from the copy's sign mask with the row mask as an
-// immediate.  m_j(u) is min1 except at the row's minimum, handled by a predicated add
+// immediate; BCH_RM receives it in bit 31 (popc << 31: one operation, no select).  m_j(u) is min1 except at the row's minimum, handled by a predicated add
 // of (v2 - v1) -- this keeps min/max/compare work on the ALU pipe down to ~4 operations
 // per edge and moves the additions to the FMA pipe.  With the pair knob on, the two
 // smallest magnitudes are tracked two edges at a time: with lo/hi the sorted pair,
@@ -99,7 +99,7 @@ const char *row_macros(int msg) {
 #define BCH_R1P(u, v) { const int p_ = abs(z[u]), q_ = abs(z[v]); const int lo_ = min(p_, q_); \
   m2_ = __vimin3_s32(m2_, max(m1_, lo_), max(p_, q_)); m1_ = min(m1_, lo_); }
 #define BCH_RM(SG) const int c1_ = rne_product(alpha, m1_); const int c2_ = rne_product(alpha, m2_); \
-  const bool neg_ = (SG); const int v1_ = neg_ ? -c1_ : c1_; const int dv_ = (neg_ ? -c2_ : c2_) - v1_;
+  const bool neg_ = int(SG) < 0; const int v1_ = neg_ ? -c1_ : c1_; const int dv_ = (neg_ ? -c2_ : c2_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2I(u) BCH_SV(u) = v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) BCH_R2(u)
@@ -118,7 +118,7 @@ const char *row_macros(int msg) {
   m1_ = fminf(a_, b_); m2_ = fmaxf(a_, b_); }
 #define BCH_R1P(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); const float lo_ = fminf(a_, b_); \
   m2_ = bch_min3f(m2_, fmaxf(m1_, lo_), fmaxf(a_, b_)); m1_ = fminf(m1_, lo_); }
-#define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
+#define BCH_RM(SG) const uint32_t sg_ = (SG); \
   const float v1_ = flip_sign(half_product(alpha, m1_), sg_); \
   const float dv_ = flip_sign(half_product(alpha, m2_), sg_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
@@ -139,7 +139,7 @@ const char *row_macros(int msg) {
   m1_ = fminf(a_, b_); m2_ = fmaxf(a_, b_); }
 #define BCH_R1P(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); const float lo_ = fminf(a_, b_); \
   m2_ = bch_min3f(m2_, fmaxf(m1_, lo_), fmaxf(a_, b_)); m1_ = fminf(m1_, lo_); }
-#define BCH_RM(SG) const uint32_t sg_ = (SG) ? kSign : 0u; \
+#define BCH_RM(SG) const uint32_t sg_ = (SG); \
   const float v1_ = flip_sign(alpha * m1_, sg_); const float dv_ = flip_sign(alpha * m2_, sg_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2I(u) BCH_SV(u) = v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
@@ -156,26 +156,26 @@ const char *row_macros(int msg) {
 // Macros of the split mapping (two warps per 32 frames, each owning half of the
 // variables): BCH_PS stores the half's partial (min1 with the sign parity in its sign
 // bit, min2) of row r into buffer B; BCH_Q combines both halves' partials of row r into
-// m1_, m2_ and the row's sign parity sgp_ (inside a BCH_R0 block).
+// m1_, m2_ and the row's sign parity sgp_ (bit 31; inside a BCH_R0 block).
 const char *split_macros(int msg) {
   if (msg == 2)
     return R"(
 #define BCH_PS(B, r, SG) B[((r) * 2 + BCH_H) * BCH_FS] = \
-  make_float2(__int_as_float(m1_ | int(uint32_t(SG) << 31)), __int_as_float(m2_));
+  make_float2(__int_as_float(m1_ | int(uint32_t(SG) & kSign)), __int_as_float(m2_));
 #define BCH_Q(B, r) const float2 qa_ = B[((r) * 2) * BCH_FS], qb_ = B[((r) * 2 + 1) * BCH_FS]; \
   const int xa_ = __float_as_int(qa_.x), xb_ = __float_as_int(qb_.x); \
   const int a1_ = xa_ & 0x7fffffff, b1_ = xb_ & 0x7fffffff; \
   m1_ = min(a1_, b1_); m2_ = min(max(a1_, b1_), min(__float_as_int(qa_.y), __float_as_int(qb_.y))); \
-  const uint32_t sgp_ = uint32_t(xa_ ^ xb_) >> 31;
+  const uint32_t sgp_ = uint32_t(xa_ ^ xb_);
 )";
   return R"(
 #define BCH_PS(B, r, SG) B[((r) * 2 + BCH_H) * BCH_FS] = \
-  make_float2(__uint_as_float(__float_as_uint(m1_) | (uint32_t(SG) << 31)), m2_);
+  make_float2(__uint_as_float(__float_as_uint(m1_) | (uint32_t(SG) & kSign)), m2_);
 #define BCH_Q(B, r) const float2 qa_ = B[((r) * 2) * BCH_FS], qb_ = B[((r) * 2 + 1) * BCH_FS]; \
   const uint32_t xa_ = __float_as_uint(qa_.x), xb_ = __float_as_uint(qb_.x); \
   const float a1_ = __uint_as_float(xa_ & 0x7fffffffu), b1_ = __uint_as_float(xb_ & 0x7fffffffu); \
   m1_ = fminf(a1_, b1_); m2_ = fminf(fmaxf(a1_, b1_), fminf(qa_.y, qb_.y)); \
-  const uint32_t sgp_ = (xa_ ^ xb_) >> 31;
+  const uint32_t sgp_ = xa_ ^ xb_;
 )";
 }
 
@@ -370,7 +370,7 @@ static void emit_copy_body(std::ostringstream &o, const bch_code *c, int msg, in
       sg << "(ng[" << w << "] & 0x" << std::hex << mw[w] << std::dec << "u)";
       first = false;
     }
-    sg << ") & 1u)";
+    sg << ") << 31)";
     o << "    BCH_R0";
     size_t e = 0;
     const bool pairs = jit_pairs();
@@ -494,7 +494,7 @@ static void emit_split_half(std::ostringstream &o, const bch_code *c, int msg, i
         sg << "(ng[" << w << "] & 0x" << std::hex << mw[w] << std::dec << "u)";
         first = false;
       }
-      sg << ") & 1u)";
+      sg << ") << 31)";
     }
     par[r] = sg.str();
   }
