@@ -43,8 +43,8 @@ LANE_OPS_PER_EDGE = 8  # min1/min2 (3), sign (1), output select (2), accumulate 
 # times its frames.  Set to None when the kernel changes until it is re-captured.
 JIT_DRAM_BYTES_PER_FRAME = (288.48e6 + 9.87e6) / 1.1e6
 # The same for the n = 127 specialised kernel (split mapping), from one ncu capture of
-# a 400 000-frame BCH(127,64) launch at 3 dB: 208.66 MB + 8.00 MB.
-JIT127_DRAM_BYTES_PER_FRAME = (208.66e6 + 8.00e6) / 4e5
+# a 400 000-frame BCH(127,64) launch at 3 dB: 208.24 MB + 8.27 MB.
+JIT127_DRAM_BYTES_PER_FRAME = (208.24e6 + 8.27e6) / 4e5
 CONFIG4_CODES = [(127, 64), (127, 99)]
 CONFIG4_POINTS = [2.0 + 0.5 * i for i in range(7)]
 
