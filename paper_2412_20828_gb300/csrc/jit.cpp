@@ -82,7 +82,8 @@ NvrtcApi &nvrtc() {
 // product of the whole row: the rows accumulate T[u] = sum_j sg_j alpha m_j(u) and the
 // factor sgn(z_u) is applied once per variable at the end.  sg_j is the parity of the
 // row's negative entries, taken from the copy's sign mask with the row mask as an
-// immediate; BCH_RM receives it in bit 31 (popc << 31: one operation, no select).  m_j(u) is min1 except at the row's minimum, handled by a predicated add
+// immediate; BCH_RM receives it in bit 31 (popc << 31: one operation, no select) and
+// applies it to alpha once (-alpha m rounds to exactly -(alpha m) in every format).  m_j(u) is min1 except at the row's minimum, handled by a predicated add
 // of (v2 - v1) -- this keeps min/max/compare work on the ALU pipe down to ~4 operations
 // per edge and moves the additions to the FMA pipe.  With the pair knob on, the two
 // smallest magnitudes are tracked two edges at a time: with lo/hi the sorted pair,
@@ -98,8 +99,8 @@ const char *row_macros(int msg) {
 #define BCH_R1F(u, v) { const int p_ = abs(z[u]), q_ = abs(z[v]); m1_ = min(p_, q_); m2_ = max(p_, q_); }
 #define BCH_R1P(u, v) { const int p_ = abs(z[u]), q_ = abs(z[v]); const int lo_ = min(p_, q_); \
   m2_ = __vimin3_s32(m2_, max(m1_, lo_), max(p_, q_)); m1_ = min(m1_, lo_); }
-#define BCH_RM(SG) const int c1_ = rne_product(alpha, m1_); const int c2_ = rne_product(alpha, m2_); \
-  const bool neg_ = int(SG) < 0; const int v1_ = neg_ ? -c1_ : c1_; const int dv_ = (neg_ ? -c2_ : c2_) - v1_;
+#define BCH_RM(SG) const float as_ = flip_sign(alpha, (SG)); \
+  const int v1_ = rne_product(as_, m1_); const int dv_ = rne_product(as_, m2_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2I(u) BCH_SV(u) = v1_; if (abs(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) BCH_R2(u)
@@ -118,9 +119,8 @@ const char *row_macros(int msg) {
   m1_ = fminf(a_, b_); m2_ = fmaxf(a_, b_); }
 #define BCH_R1P(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); const float lo_ = fminf(a_, b_); \
   m2_ = bch_min3f(m2_, fmaxf(m1_, lo_), fmaxf(a_, b_)); m1_ = fminf(m1_, lo_); }
-#define BCH_RM(SG) const uint32_t sg_ = (SG); \
-  const float v1_ = flip_sign(half_product(alpha, m1_), sg_); \
-  const float dv_ = flip_sign(half_product(alpha, m2_), sg_) - v1_;
+#define BCH_RM(SG) const float as_ = flip_sign(alpha, (SG)); \
+  const float v1_ = half_product(as_, m1_); const float dv_ = half_product(as_, m2_) - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2I(u) BCH_SV(u) = v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) { const float p_ = (fabsf(z[u]) - m1_) * 0x1p100f; \
@@ -139,8 +139,8 @@ const char *row_macros(int msg) {
   m1_ = fminf(a_, b_); m2_ = fmaxf(a_, b_); }
 #define BCH_R1P(u, v) { const float a_ = fabsf(z[u]), b_ = fabsf(z[v]); const float lo_ = fminf(a_, b_); \
   m2_ = bch_min3f(m2_, fmaxf(m1_, lo_), fmaxf(a_, b_)); m1_ = fminf(m1_, lo_); }
-#define BCH_RM(SG) const uint32_t sg_ = (SG); \
-  const float v1_ = flip_sign(alpha * m1_, sg_); const float dv_ = flip_sign(alpha * m2_, sg_) - v1_;
+#define BCH_RM(SG) const float as_ = flip_sign(alpha, (SG)); \
+  const float v1_ = as_ * m1_; const float dv_ = as_ * m2_ - v1_;
 #define BCH_R2(u) BCH_SV(u) += v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2I(u) BCH_SV(u) = v1_; if (fabsf(z[u]) == m1_) BCH_SV(u) += dv_;
 #define BCH_R2F(u) { const float p_ = (fabsf(z[u]) - m1_) * 0x1p100f; \
@@ -172,10 +172,9 @@ const char *split_macros(int msg) {
 #define BCH_PS(B, r, SG) B[((r) * 2 + BCH_H) * BCH_FS] = \
   make_float2(__uint_as_float(__float_as_uint(m1_) | (uint32_t(SG) & kSign)), m2_);
 #define BCH_Q(B, r) const float2 qa_ = B[((r) * 2) * BCH_FS], qb_ = B[((r) * 2 + 1) * BCH_FS]; \
-  const uint32_t xa_ = __float_as_uint(qa_.x), xb_ = __float_as_uint(qb_.x); \
-  const float a1_ = __uint_as_float(xa_ & 0x7fffffffu), b1_ = __uint_as_float(xb_ & 0x7fffffffu); \
+  const float a1_ = fabsf(qa_.x), b1_ = fabsf(qb_.x); \
   m1_ = fminf(a1_, b1_); m2_ = fminf(fmaxf(a1_, b1_), fminf(qa_.y, qb_.y)); \
-  const uint32_t sgp_ = xa_ ^ xb_;
+  const uint32_t sgp_ = __float_as_uint(qa_.x) ^ __float_as_uint(qb_.x);
 )";
 }
 
