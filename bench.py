@@ -38,13 +38,13 @@ METRIC = "frames/s & edge-updates/s on 1 GB300 at oracle-matched FER; served p50
 LANE_OPS_PER_EDGE = 8  # min1/min2 (3), sign (1), output select (2), accumulate (1), gather (1)
 # DRAM bytes per decoded frame of the specialised NMS kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a 1.1 M-frame BCH(63,36) launch:
-# 288.48 MB + 9.87 MB.  Traffic grows with the frames a launch decodes (each frame's
+# 288.41 MB + 9.63 MB.  Traffic grows with the frames a launch decodes (each frame's
 # LLRs are read once, its results written once), so a launch's traffic is this figure
 # times its frames.  Set to None when the kernel changes until it is re-captured.
-JIT_DRAM_BYTES_PER_FRAME = (288.48e6 + 9.87e6) / 1.1e6
+JIT_DRAM_BYTES_PER_FRAME = (288.41e6 + 9.63e6) / 1.1e6
 # The same for the n = 127 specialised kernel (split mapping), from one ncu capture of
-# a 400 000-frame BCH(127,64) launch at 3 dB: 208.24 MB + 8.27 MB.
-JIT127_DRAM_BYTES_PER_FRAME = (208.24e6 + 8.27e6) / 4e5
+# a 400 000-frame BCH(127,64) launch at 3 dB: 209.26 MB + 8.15 MB.
+JIT127_DRAM_BYTES_PER_FRAME = (209.26e6 + 8.15e6) / 4e5
 CONFIG4_CODES = [(127, 64), (127, 99)]
 CONFIG4_POINTS = [2.0 + 0.5 * i for i in range(7)]
 
